@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Throughput of Bob's reconciliation step on GB300: corrected-key Mbps.
+
+One step = one pass of the whole hot path over one batch: channel-LLR
+quantisation with the batch's punctured/shortened positions, then layered
+int8 decoding with per-frame early termination.  Inputs (Bob's keys, Alice's
+syndromes, QBERs, rate counts) are resident in device memory when the timed
+region starts; ``e2e`` repeats the measurement from pinned host buffers with
+the host<->device copies inside the timed region.
+
+Corrected-key Mbps = sum, over frames whose syndrome matched and whose
+decoded word equals Alice's key, of the key bits n - p - s, divided by the
+step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle on the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1903_10107_gb300 import inputs, rate  # noqa: E402
+
+DEFAULT_WORKLOAD = "n49152_mixed_q01_08"
+METRIC = "corrected-key Mbps on 1 GB300 at FER<=1e-2 and f~1.1 (QBER 1-8%); % HBM roofline"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (for small runs)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+
+class Batch:
+    """Host-side arrays of one rank's share of the workload."""
+
+    def __init__(self, w, batch, first):
+        self.w = w
+        self.base = w.base()
+        self.xa, self.yb, self.q = w.frames(batch, first)
+        self.B = batch
+        if w.mixed_rate:
+            self.n_punct, self.n_short = rate.plan(w.n, w.m, self.q, w.target_f)
+            self.tiebreak = inputs.tiebreak_permutation(w.n, w.code_seed)
+        else:
+            self.n_punct = np.zeros(batch, np.int32)
+            self.n_short = np.zeros(batch, np.int32)
+            self.tiebreak = None
+        self.key_bits = rate.key_bits(w.n, self.n_punct, self.n_short)
+        self.f = rate.efficiency(w.n, w.m, self.n_punct, self.n_short, self.q)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    for fn in ("decode_int8.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1903_10107_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, launch_frames: int):
+    """DRAM bytes per launch from the committed ncu summary of the decode
+    kernel, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"decode_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    msha = re.search(r"kernel_sha:\s*([0-9a-f]+)", txt)
+    mtr = re.search(r"dram_bytes_per_frame:\s*([0-9.eE+]+)", txt)
+    if not msha or not mtr or msha.group(1) != kernel_sources_sha():
+        return None
+    return float(mtr.group(1)) * launch_frames
+
+
+# ----------------------------------------------------------------- reference
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import core as orc
+    w = inputs.WORKLOADS[args.workload]
+    B = args.batch or w.batch
+    # size a per-step sample of about (cpu_seconds / (steps + warmup)) of oracle time
+    per_step = max(2.0, args.cpu_seconds * 4 / max(1, args.steps + args.warmup))
+    res = cpu_oracle_measure(w, B, per_step, orc, steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": "Mbps", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": w.name, "frames_per_step": res["frames"], "n": w.n, "max_iter": w.max_iter},
+        "cpu_baseline": {"value": res["value"], "unit": "Mbps", "cores": res["cores"], "kind": "oracle",
+                         "sample": res["sample"]},
+        "e2e": {"value": res["value"], "unit": "Mbps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_measure(w, B, seconds, orc, steps=1, warmup=0):
+    """Time the oracle on the first frames of the workload, sized to ~seconds per step."""
+    probe = min(B, max(1, orc.num_cores()))
+    bt = Batch(w, probe, 0)
+    n = w.n
+    t0 = time.time()
+    _oracle_decode(bt, orc)
+    dt = max(time.time() - t0, 1e-3)
+    k = int(min(B, max(probe, probe * seconds / dt)))
+    bt = Batch(w, k, 0)
+    for _ in range(warmup if warmup else 0):
+        _oracle_decode(bt, orc, limit=min(k, probe))
+    times, corr_bits, cores = [], 0, 1
+    for _ in range(max(1, steps)):
+        t0 = time.time()
+        bits, iters, ok, cores = _oracle_decode(bt, orc)
+        times.append(time.time() - t0)
+    xa_u = inputs.unpack_bits(bt.xa, n)
+    corr = ok.astype(bool) & np.all(bits == xa_u, axis=1)
+    corr_bits = int(bt.key_bits[corr].sum())
+    t = float(np.mean(times))
+    return {"value": corr_bits / t / 1e6, "ms_per_step": t * 1e3, "cores": int(cores), "frames": k,
+            "sample": f"first {k} of {B} frames of {w.name}, {len(times)} timed pass(es), "
+                      f"mean {t:.2f} s/pass, FER {1 - corr.mean():.3f}"}
+
+
+def _oracle_decode(bt, orc, limit=None):
+    from oracle import rate as orate
+    w = bt.w
+    k = bt.B if limit is None else limit
+    xa_u = inputs.unpack_bits(bt.xa[:k], w.n)
+    yb_u = inputs.unpack_bits(bt.yb[:k], w.n)
+    syn = orc.syndrome(bt.base, w.Z, xa_u)
+    st = kn = None
+    if w.mixed_rate:
+        rk = orate.position_rank(bt.base, w.Z, bt.tiebreak) if not hasattr(bt, "_orank") else bt._orank
+        bt._orank = rk
+        st = np.stack([orate.position_states(rk, int(bt.n_punct[f]), int(bt.n_short[f])) for f in range(k)])
+        kn = xa_u
+    llr = orc.llr_frames(yb_u, bt.q[:k], st, kn)
+    bits, iters, ok, used = orc.decode(bt.base, w.Z, llr, syn, w.max_iter)
+    return bits, iters, ok, used
+
+
+# ---------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1903_10107_gb300 import native
+    from paper_1903_10107_gb300.pipeline import Reconciler
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = inputs.WORKLOADS[args.workload]
+    B = args.batch or w.batch
+    bt = Batch(w, B, rank * B)  # weak scaling: every rank its own B frames
+    rec = Reconciler(bt.base, w.Z, bt.tiebreak, dev)
+    code = rec.code
+    # Alice's syndromes (her side of the protocol; computed once, outside the step)
+    d_xa = torch.from_numpy(bt.xa).to(dev)
+    d_syn = code.syndrome(d_xa)
+    d_yb = torch.from_numpy(bt.yb).to(dev)
+    d_q = torch.from_numpy(bt.q).to(dev)
+    mixed = w.mixed_rate
+    d_np = torch.from_numpy(bt.n_punct).to(dev) if mixed else None
+    d_ns = torch.from_numpy(bt.n_short).to(dev) if mixed else None
+    d_kn = d_xa if mixed else None
+    code.reserve(B)
+    out = (torch.empty((B, code.nbytes), dtype=torch.uint8, device=dev),
+           torch.empty((B,), dtype=torch.int32, device=dev),
+           torch.empty((B,), dtype=torch.uint8, device=dev))
+
+    def step():
+        return rec.reconcile(d_yb, d_syn, d_q, w.max_iter, d_np, d_ns, d_kn, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    l0 = native.ldpc_launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = native.ldpc_launch_count() - l0
+    barrier()
+    clk = clocks.stop()
+    step_s = ev0.elapsed_time(ev1) / 1e3 / args.steps
+
+    bits, iters, ok = (t.cpu().numpy() for t in out)
+    xa_bits = inputs.unpack_bits(bt.xa, w.n)
+    got_bits = inputs.unpack_bits(bits, w.n)
+    corr = ok.astype(bool) & np.all(got_bits == xa_bits, axis=1)
+    corr_key = float(bt.key_bits[corr].sum())
+    all_key = float(bt.key_bits.sum())
+
+    # decode kernel alone, for the roofline (same stream, CUDA events)
+    llr = code.llr_from_bsc(d_yb, d_q, rank=rec.rank if mixed else None, n_short=d_ns, n_punct=d_np,
+                            known=d_kn)
+    for _ in range(2):
+        code.decode(llr, d_syn, w.max_iter, out=out)
+    torch.cuda.synchronize()
+    reps = max(3, args.steps)
+    ev0.record(stream)
+    for _ in range(reps):
+        code.decode(llr, d_syn, w.max_iter, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dec_s = ev0.elapsed_time(ev1) / 1e3 / reps
+    it_sum = float(iters.astype(np.int64).sum())
+    io_bytes = B * (w.n + code.mbytes + code.nbytes + 4 + 1)
+    alg_bytes = it_sum * 2.0 * code.edges + io_bytes
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / dec_s / 1e9
+
+    # end to end through the public API from pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_yb, h_syn, h_q = pin(bt.yb), pin(d_syn.cpu().numpy()), pin(bt.q)
+    h_np = pin(bt.n_punct) if mixed else None
+    h_ns = pin(bt.n_short) if mixed else None
+    h_kn = pin(bt.xa) if mixed else None
+    for _ in range(max(1, args.warmup)):
+        rec.reconcile_host(h_yb, h_syn, h_q, w.max_iter, h_np, h_ns, h_kn)
+    torch.cuda.synchronize()
+    e2e_steps = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res, h2d, d2h = rec.reconcile_host(h_yb, h_syn, h_q, w.max_iter, h_np, h_ns, h_kn)
+        torch.cuda.current_stream(dev).synchronize()  # the caller reads the results
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e_bits = inputs.unpack_bits(res[0].numpy(), w.n)
+    e_corr = res[2].numpy().astype(bool) & np.all(e_bits == xa_bits, axis=1)
+    e_key = float(bt.key_bits[e_corr].sum())
+
+    # max over ranks, sums over ranks
+    vals = np.array([step_s, e2e_s, corr_key, all_key, e_key, dec_s], dtype=np.float64)
+    if dist is not None:
+        t = torch.from_numpy(vals).to(dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        vals_max, vals_sum = tmax.cpu().numpy(), t.cpu().numpy()
+    else:
+        vals_max = vals_sum = vals
+    step_max, e2e_max = vals_max[0], vals_max[1]
+    corr_tot, all_tot, e_tot = vals_sum[2], vals_sum[3], vals_sum[4]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import core as orc
+        r = cpu_oracle_measure(w, B, args.cpu_seconds, orc)
+        cpu = {"value": r["value"], "unit": "Mbps", "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+
+    if rank != 0:
+        return
+    traffic = profiled_traffic(w.name, B)
+    line = {
+        "metric": METRIC,
+        "value": corr_tot / step_max / 1e6,
+        "unit": "Mbps",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_max * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int8",
+        "data": "synthetic",
+        "config": {
+            "workload": w.name, "frames": B * world, "n": w.n, "m": w.m, "Z": w.Z, "max_iter": w.max_iter,
+            "qber": list(w.qber) if isinstance(w.qber, tuple) else w.qber,
+            "l2": "inputs larger than L2 (LLRs alone %.0f MB per rank)" % (B * w.n / 1e6),
+            "parallelism": f"frames sharded over {world} GPU(s), no collective on the data path",
+        },
+        "processed_key_mbps": all_tot / step_max / 1e6,
+        "fer": 1.0 - float(corr.mean()),
+        "efficiency_f_mean": float(np.mean(bt.f)),
+        "iters_mean": float(iters.mean()),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "decode_kernel", "kernel_ms": dec_s * 1e3,
+                     "algorithmic_bytes": alg_bytes},
+        "e2e": {"value": e_tot / e2e_max / 1e6, "unit": "Mbps", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "paper_context": "60 Mbps at f~1.1 on an Intel i7-6700HQ (section 4.2, Table 2), other codes and hardware",
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

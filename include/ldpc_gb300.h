@@ -1,0 +1,159 @@
+/*
+ * ldpc_gb300.h -- C ABI of the GB300 (sm_103a) quantised LDPC reconciliation
+ * decoder.
+ *
+ * The decoder is the paper's (Mao, Li, Han, Guo, "High Throughput and Low Cost
+ * LDPC Reconciliation for Quantum Key Distribution"): layered belief
+ * propagation (section 2) on quasi-cyclic codes (section 4.1) with 8-bit
+ * messages (section 3.1), the improved RCBP check-node table of Algorithm 1
+ * (section 3.2), the saturation-oriented variable-node rule of Algorithm 2
+ * (section 3.3) and a parity-check stopping test after every iteration
+ * (section 2), run syndrome-based: Bob decodes his key against Alice's
+ * syndrome.
+ *
+ * General rules for every entry point:
+ *   - Pointers marked "device" are CUDA device pointers; "host" pointers are
+ *     ordinary host memory.  The caller owns every input and output buffer.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     work is enqueued on it and the call returns without synchronising,
+ *     except where a function says otherwise.
+ *   - Return value: LDPC_OK (0) or a negative LDPC_E* code.  Nothing is
+ *     thrown across the ABI.  ldpc_last_error() gives a message for the most
+ *     recent failure on the calling thread.
+ *   - Bit vectors are packed LSB-first: bit j of a frame is bit (j & 7) of
+ *     byte (j >> 3); a frame of n bits takes ceil(n/8) bytes.
+ *   - Circulant convention: base entry s >= 0 at block (i, k) connects check
+ *     row r of block row i to variable node k*Z + ((r + s) mod Z).
+ *   - A code handle owns its device tables and a message scratch arena that
+ *     grows on demand (cudaMalloc) and is freed by ldpc_code_destroy.  Two
+ *     decodes that use one handle must not run concurrently on different
+ *     streams; use one handle per concurrent stream.
+ */
+#ifndef LDPC_GB300_H
+#define LDPC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LDPC_OK 0
+#define LDPC_EINVAL (-1)      /* bad argument: dimensions, shift >= Z, NULL pointer, size */
+#define LDPC_ENOMEM (-2)      /* device allocation failed */
+#define LDPC_ECUDA (-3)       /* a CUDA call or kernel launch failed (see ldpc_last_error) */
+#define LDPC_EUNSUPPORTED (-4) /* shape outside what the kernels are built for */
+#define LDPC_EKERNEL (-5)     /* a kernel reported an internal bound violation */
+
+typedef struct ldpc_code ldpc_code;
+
+/* Create a code from a quasi-cyclic base matrix (section 4.1: every nonzero
+ * base entry becomes a Z x Z cyclically shifted identity, every zero entry
+ * an all-zero block).
+ *   base : host, int32[Mb][Nb] row-major; -1 = zero block, else shift in [0, Z).
+ *   Mb, Nb, Z : base dimensions and lifting size; n = Nb*Z, m = Mb*Z.
+ *   out  : receives the new handle.
+ * One block row is one layer of the layered schedule (section 2).  Row degrees
+ * up to 64 are supported.  Errors: LDPC_EINVAL (dims <= 0, shift out of range,
+ * NULL), LDPC_EUNSUPPORTED (a row degree above 64 or n*4 bytes of state per
+ * frame group beyond shared memory), LDPC_ENOMEM, LDPC_ECUDA. */
+int ldpc_code_create(const int32_t* base, int Mb, int Nb, int Z, ldpc_code** out);
+
+/* Free the handle, its tables and its scratch arena (synchronises the device). */
+void ldpc_code_destroy(ldpc_code* code);
+
+/* n, m, edges per frame (number of ones in H) and the largest row degree.
+ * Any output pointer may be NULL. */
+int ldpc_code_info(const ldpc_code* code, int* n, int* m, int64_t* edges, int* max_row_deg);
+
+/* Grow the scratch arena for decodes of up to `batch` frames now, so that
+ * later calls allocate nothing (needed before capturing a decode in a CUDA
+ * graph).  Synchronous. */
+int ldpc_code_reserve(ldpc_code* code, int batch);
+
+/* Channel LLRs of section 3.1 for a binary symmetric channel, quantised to
+ * int8: for a key position, round-half-away(ln((1-q_f)/q_f) * scale) clamped
+ * to 127, positive for a received 0; punctured positions 0; shortened
+ * positions +127 (known bit 0) or -127 (known bit 1).  Rate adaptation of
+ * section 4.1: with `rank` given, position j of frame f is shortened when
+ * rank[j] < n_short[f], punctured when n_short[f] <= rank[j] <
+ * n_short[f] + n_punct[f], a key bit otherwise.
+ *   bob_bits : device, uint8[batch][ceil(n/8)] Bob's key.
+ *   qber     : device, double[batch] per-frame QBER in (0, 0.5).
+ *   rank     : device, int32[n] puncturing order, or NULL (all key bits).
+ *   n_short, n_punct : device, int32[batch], or NULL (zero).
+ *   known    : device, uint8[batch][ceil(n/8)] values of shortened positions
+ *              (only those positions are read), or NULL when n_short is NULL.
+ *   scale    : LSB per nat (8.0 for the workloads of this library).
+ *   llr_out  : device, int8[batch][n]. */
+int ldpc_llr_from_bsc(const ldpc_code* code, const uint8_t* bob_bits, const double* qber, const int32_t* rank,
+                      const int32_t* n_short, const int32_t* n_punct, const uint8_t* known, int batch,
+                      double scale, int8_t* llr_out, void* stream);
+
+/* Syndrome s = H x (mod 2) of a batch of packed bit vectors: the message
+ * Alice sends in the syndrome-based protocol (section 4.1).
+ *   bits    : device, uint8[batch][ceil(n/8)].
+ *   syn_out : device, uint8[batch][ceil(m/8)]. */
+int ldpc_syndrome(const ldpc_code* code, const uint8_t* bits, int batch, uint8_t* syn_out, void* stream);
+
+/* Layered decoding of a batch against target syndromes (sections 2 and 3):
+ * each iteration runs every block row in order; per check row, L_ji =
+ * sat8(E_j - L_ij) (Eq. 8), sign = syndrome sign x product of the other
+ * signs (Eq. 1), magnitude = repeated box-plus of the other magnitudes with
+ * the tau table of Algorithm 1 (Eq. 7, folded forward-backward in ascending
+ * variable order), E_j = sat8(L_ji + L_ij) unless |E_j| = 127 (Algorithm 2);
+ * after every iteration the parity checks are tested with the latest E_j and
+ * a frame stops at its first match (section 2).
+ *   llr_in          : device, int8[batch][n] channel LLRs (e.g. from
+ *                     ldpc_llr_from_bsc; 0 = punctured, +-127 = shortened).
+ *   target_syndrome : device, uint8[batch][ceil(m/8)].
+ *   batch >= 0, max_iter >= 1.
+ *   out_bits  : device, uint8[batch][ceil(n/8)] hard decisions (E_j < 0 -> 1)
+ *               at the first matching iteration, or after max_iter.
+ *   out_iters : device, int32[batch] iterations run (1..max_iter).
+ *   out_ok    : device, uint8[batch] 1 if the syndrome matched.
+ * Results are bit-exact to the reference CPU decoder and independent of the
+ * batch composition. */
+int ldpc_decode_batch(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome, int batch,
+                      int max_iter, uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, void* stream);
+
+/* ldpc_decode_batch with per-iteration, per-layer check-node tables: the
+ * magnitude m from the box-plus fold becomes
+ *   m' = clamp(((m * scale_q4[t][i] + 8) >> 4) - offset_q[t][i], 0, 127)
+ * for iteration t (0-based) and layer i.  scale 16 / offset 0 is the plain
+ * decoder; tables are the integer form of the scaled/offset check-node
+ * corrections the paper lists as alternatives in section 2 (OMS/NMS).
+ *   scale_q4 : device, uint8[max_iter][Mb], or NULL (all 16).
+ *   offset_q : device, int8[max_iter][Mb], or NULL (all 0). */
+int ldpc_decode_batch_ex(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome,
+                         int batch, int max_iter, const uint8_t* scale_q4, const int8_t* offset_q,
+                         uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, void* stream);
+
+/* ldpc_decode_batch with an explicit frame-group width: `words` 32-bit words
+ * of four int8 lanes per check row and CTA (1, 2 or 4, i.e. 4, 8 or 16
+ * frames per CTA); 0 picks automatically.  Results do not depend on it.
+ * Errors: LDPC_EINVAL for another value or one whose state does not fit in
+ * shared memory. */
+int ldpc_decode_batch_words(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome,
+                            int batch, int max_iter, int words, uint8_t* out_bits, int32_t* out_iters,
+                            uint8_t* out_ok, void* stream);
+
+/* Device evaluation of the check-node table of Algorithm 1 exactly as the
+ * decoder's byte-lane arithmetic computes it, for every (p, q) in
+ * [0,128)^2: out[p*128 + q].  out: device, uint8[16384].  For tests. */
+int ldpc_debug_tau_table(uint8_t* out, void* stream);
+
+/* Number of kernel launches this library has issued in this process. */
+int64_t ldpc_launch_count(void);
+
+/* Message for an error code, and the detailed message of the calling
+ * thread's most recent failure. */
+const char* ldpc_strerror(int code);
+const char* ldpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_GB300_H */

@@ -1,0 +1,322 @@
+// Layered int8 decoding of a batch of frames (sections 2 and 3).
+//
+// Work decomposition
+//   * A CTA owns a group of 4*W frames for the whole decode.  Frame 4w + l of
+//     the group sits in byte lane l of word w, so one 32-bit operation
+//     advances four frames.
+//   * E (the soft values, n bytes per frame) stays in shared memory for the
+//     whole decode: E_s[j*W + w].
+//   * L (check-to-variable messages, one byte per edge and frame) lives in a
+//     global scratch arena, edge-major with frames innermost:
+//     msg[group][(block b)*Z + row][w].  Consecutive threads handle
+//     consecutive rows, so every access of a warp is one contiguous run.
+//   * One block row is one layer.  The Z rows of a layer touch distinct
+//     variable nodes, so threads update them in parallel; layers are
+//     separated by a CTA barrier.
+//   * Per check row, the thread folds tau (Algorithm 1) forward and backward
+//     over the row's edges in ascending variable order, in registers.
+//   * After each iteration all parity checks are tested with the latest E
+//     (section 2); lanes whose syndrome matches are frozen and leave the
+//     group's stopping test; the CTA stops when every lane has stopped.
+#include "common.cuh"
+
+namespace {
+
+using namespace lanes;
+
+struct DecodeArgs {
+    const int32_t* tab;
+    int Mb, nblk, Z, n, m;
+    const int8_t* llr;
+    const uint8_t* syn;
+    int batch, max_iter;
+    const uint8_t* scale_q4;
+    const int8_t* offset_q;
+    uint8_t* out_bits;
+    int32_t* out_iters;
+    uint8_t* out_ok;
+    uint32_t* msg;
+};
+
+// m' = clamp(((m*s + 8) >> 4) - o, 0, 127) per byte, s and o the same for all
+// lanes.  Even and odd bytes are widened to 16-bit lanes: m*s <= 127*255 and
+// the later bias keep every lane below 2^16.
+__device__ __forceinline__ uint32_t apply_table(uint32_t m, uint32_t s, int o) {
+    uint32_t lo = m & 0x00FF00FFu, hi = (m >> 8) & 0x00FF00FFu;
+    lo = ((lo * s + 0x00080008u) >> 4) & 0x0FFF0FFFu;
+    hi = ((hi * s + 0x00080008u) >> 4) & 0x0FFF0FFFu;
+    const uint32_t bias = (uint32_t)(128 - o) * 0x00010001u;  // x - o + 128 in [1, 2280]
+    lo = __vmaxu2(__vminu2(lo + bias, 0x00FF00FFu), 0x00800080u) - 0x00800080u;
+    hi = __vmaxu2(__vminu2(hi + bias, 0x00FF00FFu), 0x00800080u) - 0x00800080u;
+    return lo | (hi << 8);
+}
+
+__device__ __forceinline__ int wrap(int x, int Z) { return x >= Z ? x - Z : x; }
+
+template <int DMAX, int W, bool TABLES>
+__device__ __forceinline__ void row_update(uint32_t* __restrict__ E_s, uint32_t* __restrict__ Lrow,
+                                           const int32_t* __restrict__ col, const int32_t* __restrict__ sh,
+                                           uint32_t syn_nib, int r, int d, int Z, int w, bool first,
+                                           uint32_t active, uint32_t sq, int oq) {
+    const size_t kstride = (size_t)Z * W;
+    uint32_t v[DMAX], a[DMAX], F[DMAX];
+    uint32_t S = nibble_to_high(syn_nib);  // syndrome sign of the row (reading: s_i flips the CN sign)
+#pragma unroll(DMAX)
+    for (int k = 0; k < DMAX; ++k) {
+        if (k < d) {
+            const uint32_t e = E_s[(col[k] * Z + wrap(r + sh[k], Z)) * W + w];
+            const uint32_t lo = first ? 0u : Lrow[k * kstride];
+            v[k] = sub_sat(e, lo);  // Eq. 8, saturated to int8
+            a[k] = absv(v[k]);
+            S ^= v[k];              // Eq. 1: product of signs = xor of sign bits
+        }
+    }
+    // Eq. 7 by forward-backward folding of tau over ascending variable order.
+    F[0] = a[0];
+#pragma unroll(DMAX)
+    for (int k = 1; k < DMAX - 1; ++k)
+        if (k <= d - 2) F[k] = tau(F[k - 1], a[k]);
+    uint32_t B = 0;
+#pragma unroll(DMAX)
+    for (int kk = 0; kk < DMAX; ++kk) {
+        const int k = DMAX - 1 - kk;  // edges in descending order
+        if (k < d) {
+            uint32_t mag;
+            if (d == 1) mag = kMax;                       // empty box-plus: MSG_max
+            else if (k == d - 1) mag = F[k >= 1 ? k - 1 : 0];
+            else if (k == 0) mag = B;
+            else mag = tau(F[k >= 1 ? k - 1 : 0], B);
+            if (k == d - 1) B = a[k];
+            else if (k > 0) B = tau(a[k], B);
+            if (TABLES) mag = apply_table(mag, sq, oq);
+            const uint32_t ln = apply_sign(mag, S ^ v[k]);  // own sign removed from the product
+            uint32_t* ep = &E_s[(col[k] * Z + wrap(r + sh[k], Z)) * W + w];
+            const uint32_t eo = *ep;
+            const uint32_t upd = active & ~saturated(eo);   // Algorithm 2: skip |E| = E_max
+            *ep = select(upd, add_sat(v[k], ln), eo);       // Eq. 9
+            Lrow[k * kstride] = ln;
+        }
+    }
+}
+
+template <int DMAX, int W, bool TABLES, int MAXT>
+__global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int n = A.n, m = A.m, Z = A.Z, Mb = A.Mb, nblk = A.nblk;
+    const int tab_words = 2 * Mb + 1 + 2 * nblk;
+    uint32_t* E_s = reinterpret_cast<uint32_t*>(smem);
+    int32_t* s_tab = reinterpret_cast<int32_t*>(smem + (size_t)4 * n * W);
+    uint8_t* syn_s = reinterpret_cast<uint8_t*>(s_tab + tab_words);
+    __shared__ uint32_t s_bad[W], s_active[W];
+    __shared__ int s_iters[4 * W];
+
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int w = tid % W, rt = tid / W, RT = T / W;
+    const int64_t f0 = (int64_t)blockIdx.x * 4 * W;
+    const int mbytes = (m + 7) / 8;
+
+    for (int i = tid; i < tab_words; i += T) s_tab[i] = A.tab[i];
+    for (int idx = tid; idx < n * W; idx += T) {
+        const int j = idx / W, ww = idx % W;
+        uint32_t word = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int64_t f = f0 + 4 * ww + l;
+            if (f < A.batch) word |= (uint32_t)(uint8_t)A.llr[f * n + j] << (8 * l);
+        }
+        E_s[idx] = word;
+    }
+    for (int idx = tid; idx < m * W; idx += T) {
+        const int c = idx / W, ww = idx % W;
+        uint32_t nib = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int64_t f = f0 + 4 * ww + l;
+            if (f < A.batch) nib |= ((A.syn[f * mbytes + (c >> 3)] >> (c & 7)) & 1u) << l;
+        }
+        syn_s[idx] = (uint8_t)nib;
+    }
+    if (tid < W) {
+        uint32_t act = 0;
+        for (int l = 0; l < 4; ++l)
+            if (f0 + 4 * tid + l < A.batch) act |= 0xFFu << (8 * l);
+        s_active[tid] = act;
+        s_bad[tid] = 0;
+    }
+    if (tid < 4 * W) s_iters[tid] = 0;
+    __syncthreads();
+
+    const int32_t* deg = s_tab;
+    const int32_t* off = s_tab + Mb;
+    const int32_t* col = s_tab + 2 * Mb + 1;
+    const int32_t* sh = col + nblk;
+    uint32_t* msg = A.msg + (size_t)blockIdx.x * nblk * Z * W;
+
+    for (int t = 1; t <= A.max_iter; ++t) {
+        const uint32_t active = s_active[w];
+        for (int i = 0; i < Mb; ++i) {  // one block row = one layer, in order
+            const int d = deg[i], b0 = off[i];
+            uint32_t sq = 16;
+            int oq = 0;
+            if (TABLES) {
+                if (A.scale_q4) sq = A.scale_q4[(size_t)(t - 1) * Mb + i];
+                if (A.offset_q) oq = A.offset_q[(size_t)(t - 1) * Mb + i];
+            }
+            if (d > 0) {
+                for (int r = rt; r < Z; r += RT)
+                    row_update<DMAX, W, TABLES>(E_s, msg + ((size_t)b0 * Z + r) * W + w, col + b0, sh + b0,
+                                                syn_s[(i * Z + r) * W + w], r, d, Z, w, t == 1, active, sq, oq);
+            }
+            __syncthreads();
+        }
+        // stopping test: every parity check with the latest E (section 2)
+        uint32_t bad = 0;
+        for (int c = rt; c < m; c += RT) {
+            const int i = c / Z, r = c - i * Z, d = deg[i], b0 = off[i];
+            uint32_t p = nibble_to_high(syn_s[c * W + w]);
+            for (int k = 0; k < d; ++k) p ^= E_s[(col[b0 + k] * Z + wrap(r + sh[b0 + k], Z)) * W + w];
+            bad |= p;
+        }
+        bad &= kHigh;
+#pragma unroll
+        for (int o = 16; o >= W; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        if ((tid & 31) < W && bad) atomicOr(&s_bad[w], bad);
+        __syncthreads();
+        if (tid < W) {
+            const uint32_t failing = spread(s_bad[tid]);
+            const uint32_t act = s_active[tid];
+            const uint32_t newly = act & ~failing;
+            for (int l = 0; l < 4; ++l)
+                if ((newly >> (8 * l)) & 0xFFu) s_iters[4 * tid + l] = t;
+            s_active[tid] = act & failing;
+            s_bad[tid] = 0;
+        }
+        __syncthreads();
+        uint32_t live = 0;
+#pragma unroll
+        for (int ww = 0; ww < W; ++ww) live |= s_active[ww];
+        if (!live) break;
+    }
+
+    if (tid < 4 * W) {
+        const int64_t f = f0 + tid;
+        if (f < A.batch) {
+            const int it = s_iters[tid];
+            A.out_iters[f] = it ? it : A.max_iter;
+            A.out_ok[f] = it ? 1 : 0;
+        }
+    }
+    const int nb = (n + 7) / 8;
+    for (int idx = tid; idx < 4 * W * nb; idx += T) {
+        const int lane = idx / nb, b = idx - lane * nb;
+        const int64_t f = f0 + lane;
+        if (f >= A.batch) continue;
+        const int ww = lane >> 2, sbit = 8 * (lane & 3) + 7;
+        uint32_t byte = 0;
+        for (int q = 0; q < 8; ++q) {
+            const int j = 8 * b + q;
+            if (j < n) byte |= ((E_s[j * W + ww] >> sbit) & 1u) << q;
+        }
+        A.out_bits[f * nb + b] = (uint8_t)byte;
+    }
+}
+
+size_t smem_bytes(const ldpc_code* c, int W) {
+    size_t b = (size_t)4 * c->n * W + sizeof(int32_t) * (2 * c->Mb + 1 + 2 * c->nblk) + (size_t)c->m * W;
+    return (b + 15) & ~(size_t)15;
+}
+
+template <int DMAX, int W, bool TABLES>
+int launch_t(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t st) {
+    constexpr int MAXT = DMAX <= 32 ? 512 : 256;
+    int T = c->Z * W;
+    if (T > MAXT) T = MAXT;
+    T = (T + 31) / 32 * 32;
+    const size_t smem = smem_bytes(c, W);
+    auto kern = decode_kernel<DMAX, W, TABLES, MAXT>;
+    LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<groups, T, smem, st>>>(A);
+    ldpc::count_launch();
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+template <int W, bool TABLES>
+int launch_w(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t st) {
+    if (c->max_deg <= 16) return launch_t<16, W, TABLES>(c, A, groups, st);
+    if (c->max_deg <= 32) return launch_t<32, W, TABLES>(c, A, groups, st);
+    return launch_t<64, W, TABLES>(c, A, groups, st);
+}
+
+int pick_words(const ldpc_code* c, int batch, int smem_limit, int sms) {
+    for (int W = 4; W >= 2; W >>= 1) {
+        const int64_t groups = (batch + 4 * W - 1) / (4 * W);
+        if ((int64_t)smem_bytes(c, W) <= smem_limit && groups >= 2 * sms) return W;
+    }
+    return 1;
+}
+
+int decode_common(const ldpc_code* c, const int8_t* llr, const uint8_t* syn, int batch, int max_iter,
+                  const uint8_t* sq, const int8_t* oq, uint8_t* bits, int32_t* iters, uint8_t* ok,
+                  void* stream, int force_words) {
+    using ldpc::fail;
+    if (!c) return fail(LDPC_EINVAL, "decode: NULL code");
+    if (batch < 0) return fail(LDPC_EINVAL, "decode: negative batch");
+    if (max_iter < 1) return fail(LDPC_EINVAL, "decode: max_iter must be >= 1");
+    if (batch == 0) return LDPC_OK;
+    if (!llr || !syn || !bits || !iters || !ok) return fail(LDPC_EINVAL, "decode: NULL buffer");
+    const int smem_limit = ldpc::max_dyn_smem(c->device);
+    if ((int64_t)smem_bytes(c, 1) > smem_limit)
+        return fail(LDPC_EUNSUPPORTED, "decode: soft values of four frames exceed shared memory");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    int W = force_words > 0 ? force_words : pick_words(c, batch, smem_limit, sms);
+    if ((W != 1 && W != 2 && W != 4) || (int64_t)smem_bytes(c, W) > smem_limit)
+        return fail(LDPC_EINVAL, "decode: unsupported words per row");
+    const int64_t groups = (batch + 4 * W - 1) / (4 * W);
+    if (groups > 0x7FFFFFFF) return fail(LDPC_EINVAL, "decode: batch too large");
+    const size_t need = (size_t)groups * 4 * W * (size_t)c->edges;
+    int rc = ldpc::ensure_arena(const_cast<ldpc_code*>(c), need);
+    if (rc) return rc;
+    DecodeArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, llr, syn, batch, max_iter, sq, oq, bits, iters, ok,
+                 reinterpret_cast<uint32_t*>(c->arena)};
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool tables = sq || oq;
+    if (W == 1) return tables ? launch_w<1, true>(c, A, (int)groups, st) : launch_w<1, false>(c, A, (int)groups, st);
+    if (W == 2) return tables ? launch_w<2, true>(c, A, (int)groups, st) : launch_w<2, false>(c, A, (int)groups, st);
+    return tables ? launch_w<4, true>(c, A, (int)groups, st) : launch_w<4, false>(c, A, (int)groups, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ldpc_decode_batch(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome, int batch,
+                      int max_iter, uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, void* stream) {
+    return decode_common(code, llr_in, target_syndrome, batch, max_iter, nullptr, nullptr, out_bits, out_iters,
+                         out_ok, stream, 0);
+}
+
+int ldpc_decode_batch_ex(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome,
+                         int batch, int max_iter, const uint8_t* scale_q4, const int8_t* offset_q,
+                         uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, void* stream) {
+    return decode_common(code, llr_in, target_syndrome, batch, max_iter, scale_q4, offset_q, out_bits, out_iters,
+                         out_ok, stream, 0);
+}
+
+// Decode with an explicit number of 32-bit words (4 frames each) per check
+// row and CTA: 1, 2 or 4.  Used by the autotuner; 0 picks automatically.
+int ldpc_decode_batch_words(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome,
+                            int batch, int max_iter, int words, uint8_t* out_bits, int32_t* out_iters,
+                            uint8_t* out_ok, void* stream) {
+    return decode_common(code, llr_in, target_syndrome, batch, max_iter, nullptr, nullptr, out_bits, out_iters,
+                         out_ok, stream, words);
+}
+
+int ldpc_code_reserve(ldpc_code* code, int batch) {
+    if (!code || batch < 0) return ldpc::fail(LDPC_EINVAL, "ldpc_code_reserve: bad argument");
+    const size_t need = (size_t)((batch + 15) / 16) * 16 * (size_t)code->edges;
+    return ldpc::ensure_arena(code, need);
+}
+
+}  // extern "C"

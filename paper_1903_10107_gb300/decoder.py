@@ -1,0 +1,137 @@
+"""PyTorch front end of the decoder library.
+
+``QCCode`` wraps one code handle.  Its methods check device, dtype, shape and
+contiguity of torch tensors, allocate outputs with torch (so device memory
+comes from PyTorch's caching allocator) and call the C ABI on the current
+CUDA stream.  Every computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import native
+
+
+def _dev_ptr(t: torch.Tensor | None, name: str, dtype, device, shape=None) -> int:
+    if t is None:
+        return None
+    if not t.is_cuda or t.device != device:
+        raise ValueError(f"{name} must be a CUDA tensor on {device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+class QCCode:
+    """A quasi-cyclic LDPC code (section 4.1) resident on one GPU.
+
+    ``base`` is ``int32[Mb][Nb]`` with ``-1`` for zero blocks and shifts in
+    ``[0, Z)``; row ``r`` of block row ``i`` connects to variable
+    ``k*Z + (r + base[i, k]) mod Z``."""
+
+    def __init__(self, base, Z: int, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        base = np.ascontiguousarray(base, dtype=np.int32)
+        if base.ndim != 2:
+            raise ValueError("base must be a 2-D matrix")
+        self.base = base
+        self.Mb, self.Nb = base.shape
+        self.Z = int(Z)
+        with torch.cuda.device(self.device):
+            self.handle = native.ldpc_code_create(base.ctypes.data, self.Mb, self.Nb, self.Z)
+        self.n, self.m, self.edges, self.max_row_deg = native.ldpc_code_info(self.handle)
+        self.nbytes = (self.n + 7) // 8
+        self.mbytes = (self.m + 7) // 8
+
+    def close(self):
+        if getattr(self, "handle", None):
+            native.ldpc_code_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def reserve(self, batch: int) -> None:
+        with torch.cuda.device(self.device):
+            native.ldpc_code_reserve(self.handle, int(batch))
+
+    # ------------------------------------------------------------ kernels
+    def syndrome(self, bits: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """H x mod 2 of packed bits ``uint8[B][ceil(n/8)]`` -> ``uint8[B][ceil(m/8)]``."""
+        B = bits.shape[0]
+        _dev_ptr(bits, "bits", torch.uint8, self.device, (B, self.nbytes))
+        if out is None:
+            out = torch.empty((B, self.mbytes), dtype=torch.uint8, device=self.device)
+        _dev_ptr(out, "out", torch.uint8, self.device, (B, self.mbytes))
+        native.ldpc_syndrome(self.handle, bits.data_ptr(), B, out.data_ptr(), self._stream())
+        return out
+
+    def llr_from_bsc(self, bob_bits, qber, rank=None, n_short=None, n_punct=None, known=None, scale: float = 8.0,
+                     out=None) -> torch.Tensor:
+        """Quantised channel LLRs ``int8[B][n]`` (section 3.1) with punctured and
+        shortened positions (section 4.1)."""
+        B = bob_bits.shape[0]
+        _dev_ptr(bob_bits, "bob_bits", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(qber, "qber", torch.float64, self.device, (B,))
+        rp = _dev_ptr(rank, "rank", torch.int32, self.device, (self.n,))
+        sp = _dev_ptr(n_short, "n_short", torch.int32, self.device, (B,))
+        pp = _dev_ptr(n_punct, "n_punct", torch.int32, self.device, (B,))
+        kp = _dev_ptr(known, "known", torch.uint8, self.device, (B, self.nbytes))
+        if out is None:
+            out = torch.empty((B, self.n), dtype=torch.int8, device=self.device)
+        _dev_ptr(out, "out", torch.int8, self.device, (B, self.n))
+        native.ldpc_llr_from_bsc(self.handle, bob_bits.data_ptr(), qber.data_ptr(), rp, sp, pp, kp, B, float(scale),
+                                 out.data_ptr(), self._stream())
+        return out
+
+    def decode(self, llr: torch.Tensor, syndrome: torch.Tensor, max_iter: int, scale_q4=None, offset_q=None,
+               words: int = 0, out=None):
+        """Layered int8 decoding; returns ``(bits uint8[B][ceil(n/8)], iters
+        int32[B], ok uint8[B])``."""
+        B = llr.shape[0]
+        _dev_ptr(llr, "llr", torch.int8, self.device, (B, self.n))
+        _dev_ptr(syndrome, "syndrome", torch.uint8, self.device, (B, self.mbytes))
+        sq = _dev_ptr(scale_q4, "scale_q4", torch.uint8, self.device, (max_iter, self.Mb))
+        oq = _dev_ptr(offset_q, "offset_q", torch.int8, self.device, (max_iter, self.Mb))
+        if out is None:
+            out = (torch.empty((B, self.nbytes), dtype=torch.uint8, device=self.device),
+                   torch.empty((B,), dtype=torch.int32, device=self.device),
+                   torch.empty((B,), dtype=torch.uint8, device=self.device))
+        bits, iters, ok = out
+        _dev_ptr(bits, "out bits", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(iters, "out iters", torch.int32, self.device, (B,))
+        _dev_ptr(ok, "out ok", torch.uint8, self.device, (B,))
+        st = self._stream()
+        with torch.cuda.device(self.device):
+            if sq is not None or oq is not None:
+                if words:
+                    raise ValueError("words cannot be combined with tables")
+                native.ldpc_decode_batch_ex(self.handle, llr.data_ptr(), syndrome.data_ptr(), B, int(max_iter), sq, oq,
+                                            bits.data_ptr(), iters.data_ptr(), ok.data_ptr(), st)
+            elif words:
+                native.ldpc_decode_batch_words(self.handle, llr.data_ptr(), syndrome.data_ptr(), B, int(max_iter),
+                                               int(words), bits.data_ptr(), iters.data_ptr(), ok.data_ptr(), st)
+            else:
+                native.ldpc_decode_batch(self.handle, llr.data_ptr(), syndrome.data_ptr(), B, int(max_iter),
+                                         bits.data_ptr(), iters.data_ptr(), ok.data_ptr(), st)
+        return bits, iters, ok
+
+
+def tau_table_device(device=None) -> torch.Tensor:
+    """The decoder's byte-lane tau evaluated on the GPU for all (p, q) < 128."""
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    out = torch.empty(128 * 128, dtype=torch.uint8, device=device)
+    with torch.cuda.device(device):
+        native.ldpc_debug_tau_table(out.data_ptr(), torch.cuda.current_stream(device).cuda_stream)
+    return out.view(128, 128)

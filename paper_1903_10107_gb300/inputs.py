@@ -128,16 +128,17 @@ class Workload:
             degs = degs(self)
         return qc_base_matrix(self.Mb, self.Nb, self.Z, degs, self.code_seed)
 
-    def qbers(self, batch=None) -> np.ndarray:
+    def qbers(self, batch=None, first: int = 0) -> np.ndarray:
+        """QBER of frames ``first .. first+batch-1``."""
         b = self.batch if batch is None else batch
         if isinstance(self.qber, tuple):
-            return frame_qbers(self.batch, self.qber[0], self.qber[1], self.frame_seed)[:b]
+            return frame_qbers(first + b, self.qber[0], self.qber[1], self.frame_seed)[first:first + b]
         return np.full(b, float(self.qber))
 
-    def frames(self, batch=None, first=0):
-        """Alice's keys and Bob's keys (Alice XOR noise), both packed."""
+    def frames(self, batch=None, first: int = 0):
+        """Alice's keys, Bob's keys (Alice XOR noise), both packed, and the QBERs."""
         b = self.batch if batch is None else batch
-        q = self.qbers(first + b)[first:first + b] if isinstance(self.qber, tuple) else self.qbers(b)
+        q = self.qbers(b, first)
         xa = alice_keys(b, self.n, self.frame_seed, first)
         yb = xa ^ bsc_noise(b, self.n, q, self.frame_seed, first)
         return xa, yb, q
