@@ -139,6 +139,40 @@ int ldpc_decode_batch_words(const ldpc_code* code, const int8_t* llr_in, const u
                             int batch, int max_iter, int words, uint8_t* out_bits, int32_t* out_iters,
                             uint8_t* out_ok, void* stream);
 
+/* Persistent mixed-rate reconciliation: ldpc_llr_from_bsc fused into the
+ * layered decoder of ldpc_decode_batch, in one launch of resident CTAs that
+ * pull frames from a device work counter (frames of different rates, QBERs
+ * and iteration counts share the mother code; section 4.1).  Every byte lane
+ * of a CTA decodes one frame at a time and, when the frame stops, takes the
+ * next one, so uneven iteration counts leave no lane idle while work remains.
+ *   bob_bits, qber, rank, n_short, n_punct, known : as in ldpc_llr_from_bsc,
+ *       indexed by frame id.
+ *   target_syndrome : device, uint8[batch][ceil(m/8)], indexed by frame id.
+ *   batch : number of frames in the per-frame arrays.
+ *   frame_list : device, int32[list_len] frame ids to decode (e.g. the frames
+ *       still failing after an interactive reveal), or NULL for 0..list_len-1
+ *       (then list_len <= batch).  Ids outside [0, batch) are skipped.
+ *   max_iter, llr_scale : iteration cap and LSB per nat.
+ *   words : 32-bit lane words per CTA (1, 2, 4; 0 = automatic).
+ *   ctas_per_sm : resident CTAs per SM (0 = as many as fit).
+ *   out_bits, out_iters, out_ok : device, indexed by frame id; entries of
+ *       frames not in the list are left untouched.
+ * Per-frame results equal ldpc_decode_batch on the LLRs of
+ * ldpc_llr_from_bsc.  Capturable in a CUDA graph once the scratch arena is
+ * large enough (ldpc_code_reserve_persistent). */
+int ldpc_reconcile_persistent(const ldpc_code* code, const uint8_t* bob_bits, const double* qber,
+                              const int32_t* rank, const int32_t* n_short, const int32_t* n_punct,
+                              const uint8_t* known, const uint8_t* target_syndrome, int batch,
+                              const int32_t* frame_list, int list_len, int max_iter, double llr_scale, int words,
+                              int ctas_per_sm, uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok,
+                              void* stream);
+
+/* Grow the scratch arena now for a persistent decode of `list_len` frames
+ * with the given `words` and `ctas_per_sm` (0 = automatic, as in
+ * ldpc_reconcile_persistent), so that the decode itself allocates nothing
+ * and can be captured in a CUDA graph.  Synchronous. */
+int ldpc_code_reserve_persistent(ldpc_code* code, int list_len, int words, int ctas_per_sm);
+
 /* Device evaluation of the check-node table of Algorithm 1 exactly as the
  * decoder's byte-lane arithmetic computes it, for every (p, q) in
  * [0,128)^2: out[p*128 + q].  out: device, uint8[16384].  For tests. */

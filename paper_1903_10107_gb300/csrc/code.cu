@@ -91,9 +91,12 @@ int ldpc_code_create(const int32_t* base, int Mb, int Nb, int Z, ldpc_code** out
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tab, c->tab_words * sizeof(int32_t));
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_tab, c->h_tab.data(), c->tab_words * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_queue, 256);
+    if (e == cudaSuccess) e = cudaMemset(c->d_queue, 0, 256);
     if (e != cudaSuccess) {
         int r = ldpc::cuda_fail(e, "ldpc_code_create: table upload");
         if (c->d_tab) cudaFree(c->d_tab);
+        if (c->d_queue) cudaFree(c->d_queue);
         delete c;
         return r;
     }
@@ -106,6 +109,7 @@ void ldpc_code_destroy(ldpc_code* c) {
     cudaDeviceSynchronize();
     if (c->d_tab) cudaFree(c->d_tab);
     if (c->arena) cudaFree(c->arena);
+    if (c->d_queue) cudaFree(c->d_queue);
     delete c;
 }
 

@@ -24,6 +24,7 @@ struct ldpc_code {
     size_t tab_words = 0;
     void* arena = nullptr;  // message scratch
     size_t arena_bytes = 0;
+    int* d_queue = nullptr; // work counter of the persistent decoder
 };
 
 namespace ldpc {
@@ -77,59 +78,44 @@ __device__ __forceinline__ uint32_t select(uint32_t mask, uint32_t x, uint32_t y
     return (x & mask) | (y & ~mask);
 }
 
-// sat8(x - y) per byte for x, y in [-127, 127]: saturating subtraction
-// (range [-128, 127]) followed by a max with -127.
-__device__ __forceinline__ uint32_t sub_sat(uint32_t x, uint32_t y) {
-    return __vmaxs4(__vsubss4(x, y), kMin);
-}
+// |x - y| per byte, unsigned (a native byte-lane instruction).
+__device__ __forceinline__ uint32_t absdiff(uint32_t x, uint32_t y) { return __vabsdiffu4(x, y); }
 
-// sat8(x + y) per byte for x, y in [-127, 127].
-__device__ __forceinline__ uint32_t add_sat(uint32_t x, uint32_t y) {
-    return __vmaxs4(__vaddss4(x, y), kMin);
-}
+// min(x, 127) per byte for x in [0, 255].
+__device__ __forceinline__ uint32_t cap127(uint32_t x) { return (x | spread(x)) & kMax; }
 
-// |x| per byte for x in [-127, 127].
-__device__ __forceinline__ uint32_t absv(uint32_t x) {
-    const uint32_t s = spread(x);
-    return (x ^ s) + (s & kOnes);  // ~x + 1 = -x lies in [1, 127] for x in [-127, -1]
+// Bit 7 of each byte = [x < y] for unsigned bytes.  (x | 128) - (y & 127)
+// stays in [1, 255] per byte, so its bit 7 is [x mod 128 >= y mod 128]; the
+// top bits then decide as in a borrow chain.
+__device__ __forceinline__ uint32_t lt_u8(uint32_t x, uint32_t y) {
+    const uint32_t c = (x | kHigh) - (y & kMax);
+    return ((~x & y) | (~(x ^ y) & ~c)) & kHigh;
 }
 
 // tau(a, b) of Algorithm 1 per byte, for a, b in [0, 127] (= MSG_max, so the
 // input caps are the identity).
-//   l = min, g = max, d = g - l;  l > 2: l - [d<2] - [d<6];  else max(l - [d<4], 0)
-// The tests are "x >= c" read from bit 7 of x + (128 - c), which stays below
-// 256 for x <= 127.  For l <= 2 the correction is [d<4] only where l >= 1,
-// which equals the max(., 0).
+//   l = min, d = |a - b|;  l > 2: l - [d<2] - [d<6];  else max(l - [d<4], 0)
+// l = (a + b - d) / 2 (a + b <= 254 fits a byte).  The tests "x >= c" are
+// bit 7 of x + (128 - c), which stays below 256 for x <= 127.  For l <= 2
+// the correction [d<4] is applied only where l >= 1, which equals max(., 0).
 __device__ __forceinline__ uint32_t tau(uint32_t a, uint32_t b) {
-    const uint32_t m = spread(a + kHigh - b);    // a + 128 - b in [1, 255]: bit 7 = (a >= b)
-    const uint32_t l = select(m, b, a);
-    const uint32_t g = select(m, a, b);
-    const uint32_t d = g - l;                    // in [0, 127]
+    const uint32_t d = absdiff(a, b);
+    const uint32_t l = ((a + b - d) >> 1) & kMax;
     const uint32_t d_ge2 = d + 0x7E7E7E7Eu;
     const uint32_t d_ge4 = d + 0x7C7C7C7Cu;
     const uint32_t d_ge6 = d + 0x7A7A7A7Au;
     const uint32_t l_ge3 = l + 0x7D7D7D7Du;
     const uint32_t l_ge1 = l + 0x7F7F7F7Fu;
-    const uint32_t c2 = l_ge3 & ~d_ge2 & kHigh;                               // l>=3 and d<2
+    const uint32_t c2 = l_ge3 & ~d_ge2 & kHigh;                                 // l>=3 and d<2
     const uint32_t c1 = ((l_ge3 & ~d_ge6) | (~l_ge3 & ~d_ge4)) & l_ge1 & kHigh; // l>=3 ? d<6 : (l>=1 and d<4)
-    return l - (c2 >> 7) - (c1 >> 7);            // corrections <= l, no borrow
+    return l - (c2 >> 7) - (c1 >> 7);                                          // corrections <= l, no borrow
 }
 
-// -m in the bytes where bit 7 of s is set, m elsewhere; m in [0, 127].
-__device__ __forceinline__ uint32_t apply_sign(uint32_t m, uint32_t s) {
-    const uint32_t neg = (kHigh - m) ^ kHigh;    // 128 - m in [1, 128]; xor 128 gives 256 - m (0 -> 0)
-    return select(spread(s), neg, m);
-}
-
-// 0xFF in the bytes with |x| = 127 (x in [-127, 127]).
-__device__ __forceinline__ uint32_t saturated(uint32_t x) {
-    return spread(absv(x) + kOnes);              // |x| + 1 reaches 128 only for |x| = 127
-}
-
-// Four syndrome bits (bit l = frame l) -> bit 7 of byte l.  The four partial
-// products x << (7 + 7k) occupy disjoint bit ranges, so the multiply adds no
-// carries.
-__device__ __forceinline__ uint32_t nibble_to_high(uint32_t nib) { return (nib * 0x10204080u) & kHigh; }
+// Four syndrome bits (bit l = frame l) -> bit 7 of byte l.  For a 4-bit
+// input the four partial products x << (7 + 7k) occupy disjoint bit ranges,
+// so the multiply adds no carries; higher input bits would carry into the
+// upper lanes, hence the mask.
+__device__ __forceinline__ uint32_t nibble_to_high(uint32_t nib) { return ((nib & 0xFu) * 0x10204080u) & kHigh; }
 
 // Bit 7 of each byte -> bit l of a nibble.
 __device__ __forceinline__ uint32_t high_to_nibble(uint32_t x) {

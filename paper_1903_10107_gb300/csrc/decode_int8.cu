@@ -18,11 +18,12 @@
 //   * After each iteration all parity checks are tested with the latest E
 //     (section 2); lanes whose syndrome matches are frozen and leave the
 //     group's stopping test; the CTA stops when every lane has stopped.
-#include "common.cuh"
+#include "row_update.cuh"
 
 namespace {
 
 using namespace lanes;
+using ldpc_dev::RowCtx;
 
 struct DecodeArgs {
     const int32_t* tab;
@@ -38,68 +39,9 @@ struct DecodeArgs {
     uint32_t* msg;
 };
 
-// m' = clamp(((m*s + 8) >> 4) - o, 0, 127) per byte, s and o the same for all
-// lanes.  Even and odd bytes are widened to 16-bit lanes: m*s <= 127*255 and
-// the later bias keep every lane below 2^16.
-__device__ __forceinline__ uint32_t apply_table(uint32_t m, uint32_t s, int o) {
-    uint32_t lo = m & 0x00FF00FFu, hi = (m >> 8) & 0x00FF00FFu;
-    lo = ((lo * s + 0x00080008u) >> 4) & 0x0FFF0FFFu;
-    hi = ((hi * s + 0x00080008u) >> 4) & 0x0FFF0FFFu;
-    const uint32_t bias = (uint32_t)(128 - o) * 0x00010001u;  // x - o + 128 in [1, 2280]
-    lo = __vmaxu2(__vminu2(lo + bias, 0x00FF00FFu), 0x00800080u) - 0x00800080u;
-    hi = __vmaxu2(__vminu2(hi + bias, 0x00FF00FFu), 0x00800080u) - 0x00800080u;
-    return lo | (hi << 8);
-}
-
-__device__ __forceinline__ int wrap(int x, int Z) { return x >= Z ? x - Z : x; }
-
-template <int DMAX, int W, bool TABLES>
-__device__ __forceinline__ void row_update(uint32_t* __restrict__ E_s, uint32_t* __restrict__ Lrow,
-                                           const int32_t* __restrict__ col, const int32_t* __restrict__ sh,
-                                           uint32_t syn_nib, int r, int d, int Z, int w, bool first,
-                                           uint32_t active, uint32_t sq, int oq) {
-    const size_t kstride = (size_t)Z * W;
-    uint32_t v[DMAX], a[DMAX], F[DMAX];
-    uint32_t S = nibble_to_high(syn_nib);  // syndrome sign of the row (reading: s_i flips the CN sign)
-#pragma unroll(DMAX)
-    for (int k = 0; k < DMAX; ++k) {
-        if (k < d) {
-            const uint32_t e = E_s[(col[k] * Z + wrap(r + sh[k], Z)) * W + w];
-            const uint32_t lo = first ? 0u : Lrow[k * kstride];
-            v[k] = sub_sat(e, lo);  // Eq. 8, saturated to int8
-            a[k] = absv(v[k]);
-            S ^= v[k];              // Eq. 1: product of signs = xor of sign bits
-        }
-    }
-    // Eq. 7 by forward-backward folding of tau over ascending variable order.
-    F[0] = a[0];
-#pragma unroll(DMAX)
-    for (int k = 1; k < DMAX - 1; ++k)
-        if (k <= d - 2) F[k] = tau(F[k - 1], a[k]);
-    uint32_t B = 0;
-#pragma unroll(DMAX)
-    for (int kk = 0; kk < DMAX; ++kk) {
-        const int k = DMAX - 1 - kk;  // edges in descending order
-        if (k < d) {
-            uint32_t mag;
-            if (d == 1) mag = kMax;                       // empty box-plus: MSG_max
-            else if (k == d - 1) mag = F[k >= 1 ? k - 1 : 0];
-            else if (k == 0) mag = B;
-            else mag = tau(F[k >= 1 ? k - 1 : 0], B);
-            if (k == d - 1) B = a[k];
-            else if (k > 0) B = tau(a[k], B);
-            if (TABLES) mag = apply_table(mag, sq, oq);
-            const uint32_t ln = apply_sign(mag, S ^ v[k]);  // own sign removed from the product
-            uint32_t* ep = &E_s[(col[k] * Z + wrap(r + sh[k], Z)) * W + w];
-            const uint32_t eo = *ep;
-            const uint32_t upd = active & ~saturated(eo);   // Algorithm 2: skip |E| = E_max
-            *ep = select(upd, add_sat(v[k], ln), eo);       // Eq. 9
-            Lrow[k * kstride] = ln;
-        }
-    }
-}
-
-template <int DMAX, int W, bool TABLES, int MAXT>
+// Threads: tid = ((row slot) * P + half) * W + w.  The two halves of a row sit
+// W lanes apart in one warp.
+template <int HMAX, int P, int W, bool TABLES, int MAXT>
 __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int n = A.n, m = A.m, Z = A.Z, Mb = A.Mb, nblk = A.nblk;
@@ -111,7 +53,9 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
     __shared__ int s_iters[4 * W];
 
     const int tid = threadIdx.x, T = blockDim.x;
-    const int w = tid % W, rt = tid / W, RT = T / W;
+    const int w = tid % W, q = tid / W;
+    const int half = (P == 2) ? (q & 1) : 0;
+    const int rt = q / P, RT = T / (W * P), QT = T / W;
     const int64_t f0 = (int64_t)blockIdx.x * 4 * W;
     const int mbytes = (m + 7) / 8;
 
@@ -124,7 +68,7 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
             const int64_t f = f0 + 4 * ww + l;
             if (f < A.batch) word |= (uint32_t)(uint8_t)A.llr[f * n + j] << (8 * l);
         }
-        E_s[idx] = word;
+        E_s[idx] = word ^ kHigh;  // offset binary
     }
     for (int idx = tid; idx < m * W; idx += T) {
         const int c = idx / W, ww = idx % W;
@@ -150,34 +94,44 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
     const int32_t* off = s_tab + Mb;
     const int32_t* col = s_tab + 2 * Mb + 1;
     const int32_t* sh = col + nblk;
-    uint32_t* msg = A.msg + (size_t)blockIdx.x * nblk * Z * W;
+
+    RowCtx C;
+    C.E_s = E_s;
+    C.msg = A.msg + (size_t)blockIdx.x * nblk * Z * W;
+    C.Z = Z;
+    C.W = W;
+    C.w = w;
+    C.sq = 16;
+    C.oq = 0;
 
     for (int t = 1; t <= A.max_iter; ++t) {
-        const uint32_t active = s_active[w];
-        for (int i = 0; i < Mb; ++i) {  // one block row = one layer, in order
-            const int d = deg[i], b0 = off[i];
-            uint32_t sq = 16;
-            int oq = 0;
+        C.active = s_active[w];
+        C.fresh = (t == 1) ? 0xFFFFFFFFu : 0u;  // messages start at 0 (stale scratch is never read)
+        for (int i = 0; i < Mb; ++i) {          // one block row = one layer, in order
+            C.d = deg[i];
+            C.b0 = off[i];
+            C.col = col + C.b0;
+            C.sh = sh + C.b0;
             if (TABLES) {
-                if (A.scale_q4) sq = A.scale_q4[(size_t)(t - 1) * Mb + i];
-                if (A.offset_q) oq = A.offset_q[(size_t)(t - 1) * Mb + i];
+                if (A.scale_q4) C.sq = A.scale_q4[(size_t)(t - 1) * Mb + i];
+                if (A.offset_q) C.oq = A.offset_q[(size_t)(t - 1) * Mb + i];
             }
-            if (d > 0) {
-                for (int r = rt; r < Z; r += RT)
-                    row_update<DMAX, W, TABLES>(E_s, msg + ((size_t)b0 * Z + r) * W + w, col + b0, sh + b0,
-                                                syn_s[(i * Z + r) * W + w], r, d, Z, w, t == 1, active, sq, oq);
+            if (C.d > 0) {
+                for (int r0 = 0; r0 < Z; r0 += RT) {
+                    const int r = r0 + rt;
+                    const bool valid = r < Z;
+                    const uint32_t nib = valid ? syn_s[(i * Z + r) * W + w] : 0u;
+                    ldpc_dev::row_update<HMAX, P, TABLES>(C, valid ? r : 0, valid, half, nib);
+                }
             }
             __syncthreads();
         }
         // stopping test: every parity check with the latest E (section 2)
         uint32_t bad = 0;
-        for (int c = rt; c < m; c += RT) {
-            const int i = c / Z, r = c - i * Z, d = deg[i], b0 = off[i];
-            uint32_t p = nibble_to_high(syn_s[c * W + w]);
-            for (int k = 0; k < d; ++k) p ^= E_s[(col[b0 + k] * Z + wrap(r + sh[b0 + k], Z)) * W + w];
-            bad |= p;
+        for (int c = q; c < m; c += QT) {
+            const int i = c / Z, r = c - i * Z;
+            bad |= ldpc_dev::row_parity(E_s, col + off[i], sh + off[i], deg[i], r, Z, W, w, syn_s[c * W + w]);
         }
-        bad &= kHigh;
 #pragma unroll
         for (int o = 16; o >= W; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
         if ((tid & 31) < W && bad) atomicOr(&s_bad[w], bad);
@@ -213,9 +167,9 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
         if (f >= A.batch) continue;
         const int ww = lane >> 2, sbit = 8 * (lane & 3) + 7;
         uint32_t byte = 0;
-        for (int q = 0; q < 8; ++q) {
-            const int j = 8 * b + q;
-            if (j < n) byte |= ((E_s[j * W + ww] >> sbit) & 1u) << q;
+        for (int qq = 0; qq < 8; ++qq) {
+            const int j = 8 * b + qq;
+            if (j < n) byte |= ((~E_s[j * W + ww] >> sbit) & 1u) << qq;  // E < 0 <=> stored bit 7 clear
         }
         A.out_bits[f * nb + b] = (uint8_t)byte;
     }
@@ -226,14 +180,15 @@ size_t smem_bytes(const ldpc_code* c, int W) {
     return (b + 15) & ~(size_t)15;
 }
 
-template <int DMAX, int W, bool TABLES>
+template <int HMAX, int W, bool TABLES>
 int launch_t(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t st) {
-    constexpr int MAXT = DMAX <= 32 ? 512 : 256;
-    int T = c->Z * W;
+    constexpr int P = 2;
+    constexpr int MAXT = HMAX <= 16 ? 1024 : 512;
+    int T = c->Z * W * P;
     if (T > MAXT) T = MAXT;
     T = (T + 31) / 32 * 32;
     const size_t smem = smem_bytes(c, W);
-    auto kern = decode_kernel<DMAX, W, TABLES, MAXT>;
+    auto kern = decode_kernel<HMAX, P, W, TABLES, MAXT>;
     LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<groups, T, smem, st>>>(A);
     ldpc::count_launch();
@@ -241,11 +196,13 @@ int launch_t(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t s
     return LDPC_OK;
 }
 
+// Half-row length: two threads share a row, each walking ceil(d/2) edges at most.
 template <int W, bool TABLES>
 int launch_w(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t st) {
-    if (c->max_deg <= 16) return launch_t<16, W, TABLES>(c, A, groups, st);
-    if (c->max_deg <= 32) return launch_t<32, W, TABLES>(c, A, groups, st);
-    return launch_t<64, W, TABLES>(c, A, groups, st);
+    const int h = (c->max_deg + 1) / 2;
+    if (h <= 8) return launch_t<8, W, TABLES>(c, A, groups, st);
+    if (h <= 16) return launch_t<16, W, TABLES>(c, A, groups, st);
+    return launch_t<32, W, TABLES>(c, A, groups, st);
 }
 
 int pick_words(const ldpc_code* c, int batch, int smem_limit, int sms) {

@@ -1,0 +1,139 @@
+// One check row of the layered decoder (sections 2 and 3), in byte lanes.
+//
+// Storage is offset binary: a soft value E (or message L) in [-127, 127] is
+// kept as the byte E + 128, so |E - L| is one unsigned byte absolute
+// difference and the hard decision E < 0 is "bit 7 clear".
+//
+// Per edge the thread forms, from the stored E_j and L_ij (Eq. 8):
+//   a = min(|E_j - L_ij|, 127) = |sat8(E_j - L_ij)|, sign bit sv = [E_j < L_ij]
+// and packs them as av = a | sv (bit 7).  The row's sign S is the syndrome bit
+// xor every sv (Eq. 1 with the syndrome sign).  The magnitude for edge k is
+// the box-plus of the other magnitudes (Eq. 7) with tau of Algorithm 1,
+// folded forward-backward in ascending variable order:
+//   m_k = tau(F_{k-1}, B_{k+1}),  F = left fold, B = right fold.
+// The outgoing message is L_ij = (S xor sv) m and the soft value becomes
+// sat8(v + L_ij) (Eq. 9) unless |E_j| = 127 (Algorithm 2):
+//   S = 0 (same sign):     E = sv * min(a + m, 127)
+//   S = 1 (opposite sign): E = sv * (a - m)          (already in range)
+//
+// Two threads may share a row (P = 2).  Thread 0 walks edges 0..h-1 upward,
+// thread 1 walks edges d-1..h downward; both fold tau over their own walk
+// (tau is symmetric, so thread 1's fold is the right fold B), swap their
+// totals and sign parities with one shuffle each, and walk back to produce
+// their outputs.  Both threads run the same instructions.
+#pragma once
+
+#include "common.cuh"
+
+namespace ldpc_dev {
+
+using namespace lanes;
+
+__device__ __forceinline__ int wrap(int x, int Z) { return x >= Z ? x - Z : x; }
+
+// m' = clamp(((m*s + 8) >> 4) - o, 0, 127) per byte, s and o the same for all
+// lanes.  Even and odd bytes are widened to 16-bit lanes: m*s <= 127*255 and
+// the later bias keep every lane below 2^16.
+__device__ __forceinline__ uint32_t apply_table(uint32_t m, uint32_t s, int o) {
+    uint32_t lo = m & 0x00FF00FFu, hi = (m >> 8) & 0x00FF00FFu;
+    lo = ((lo * s + 0x00080008u) >> 4) & 0x0FFF0FFFu;
+    hi = ((hi * s + 0x00080008u) >> 4) & 0x0FFF0FFFu;
+    const uint32_t bias = (uint32_t)(128 - o) * 0x00010001u;  // x - o + 128 in [1, 2280]
+    lo = __vmaxu2(__vminu2(lo + bias, 0x00FF00FFu), 0x00800080u) - 0x00800080u;
+    hi = __vmaxu2(__vminu2(hi + bias, 0x00FF00FFu), 0x00800080u) - 0x00800080u;
+    return lo | (hi << 8);
+}
+
+struct RowCtx {
+    uint32_t* E_s;           // shared soft values, [n][W] words
+    uint32_t* msg;           // this CTA's messages, [(block)*Z + row][W] words
+    const int32_t* col;      // block columns of the layer (ascending)
+    const int32_t* sh;       // circulant shifts of the layer
+    int b0, d, Z, W, w;      // layer block offset and degree; lifting; words per row; my word
+    uint32_t fresh;          // lanes whose stored L is stale (treated as 0)
+    uint32_t active;         // lanes whose E may change
+    uint32_t sq;             // table scale (16 = identity)
+    int oq;                  // table offset
+};
+
+// `half` is 0 or 1 (always 0 when P == 1); `valid` false makes the thread a
+// bystander that only joins the shuffles.
+template <int HMAX, int P, bool TABLES>
+__device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, int half, uint32_t syn_nib) {
+    const int d = valid ? C.d : 0;
+    const int h = (P == 1) ? d : (d + 1) >> 1;
+    const int cnt = half ? d - h : h;           // edges walked by this thread
+    const int partner = (P == 1) ? 0 : (half ? h : d - h);
+    const int Z = C.Z, W = C.W, w = C.w;
+    const size_t kstride = (size_t)Z * W;
+    uint32_t* Lrow = C.msg + ((size_t)C.b0 * Z + r) * W + w;
+    uint32_t av[HMAX], F[HMAX];
+    uint32_t S = (half == 0 && valid) ? nibble_to_high(syn_nib) : 0u;
+
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < cnt) {
+            const int k = half ? d - 1 - j : j;
+            const uint32_t e = C.E_s[(C.col[k] * Z + wrap(r + C.sh[k], Z)) * W + w];
+            uint32_t lb = kHigh;                 // offset-binary zero
+            if (C.fresh != 0xFFFFFFFFu) lb = select(C.fresh, kHigh, Lrow[k * kstride]);
+            const uint32_t sv = lt_u8(e, lb);    // sign of E - L
+            av[j] = cap127(absdiff(e, lb)) | sv; // |sat8(E - L)| and its sign
+            S ^= sv;
+        }
+    }
+    uint32_t tot = kMax;
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < cnt) {
+            const uint32_t a = av[j] & kMax;
+            F[j] = (j == 0) ? a : tau(F[j >= 1 ? j - 1 : 0], a);
+            if (j == cnt - 1) tot = F[j];
+        }
+    }
+    uint32_t R = kMax;
+    if (P == 2) {
+        R = __shfl_xor_sync(0xffffffffu, tot, W);
+        S ^= __shfl_xor_sync(0xffffffffu, S, W);
+    }
+    bool rvalid = partner > 0;
+    const uint32_t MS = spread(S);
+
+#pragma unroll(HMAX)
+    for (int jj = 0; jj < HMAX; ++jj) {
+        const int j = HMAX - 1 - jj;
+        if (j < cnt) {
+            const int k = half ? d - 1 - j : j;
+            const uint32_t a = av[j] & kMax;
+            const uint32_t Fp = F[j >= 1 ? j - 1 : 0];
+            uint32_t m;
+            if (rvalid) m = (j == 0) ? R : tau(Fp, R);
+            else m = (j == 0) ? kMax : Fp;     // no edge beyond: left fold alone (degree 1: MSG_max)
+            if (j > 0) R = rvalid ? tau(a, R) : a;
+            rvalid = true;
+            if (TABLES) m = apply_table(m, C.sq, C.oq);
+            const uint32_t Msv = spread(av[j]);
+            const uint32_t lnew = select(Msv ^ MS, kHigh - m, kHigh | m);
+            const uint32_t c = cap127(a + m);
+            const uint32_t e_same = select(Msv, kHigh - c, kHigh | c);
+            const uint32_t e_opp = select(Msv, kHigh - a + m, kHigh + a - m);
+            uint32_t* ep = &C.E_s[(C.col[k] * Z + wrap(r + C.sh[k], Z)) * W + w];
+            const uint32_t eo = *ep;
+            const uint32_t sat = spread(absdiff(eo, kHigh) + kOnes);  // |E| = 127
+            *ep = select(C.active & ~sat, select(MS, e_opp, e_same), eo);
+            Lrow[k * kstride] = lnew;
+        }
+    }
+}
+
+// Parity of check row c (layer i, row r) against its syndrome bits: bit 7 of
+// each byte set where the lane's check fails.  Hard decision: E < 0, i.e.
+// bit 7 of the stored byte clear, so the xor of bit 7s is flipped once per edge.
+__device__ __forceinline__ uint32_t row_parity(const uint32_t* E_s, const int32_t* col, const int32_t* sh, int d,
+                                               int r, int Z, int W, int w, uint32_t syn_nib) {
+    uint32_t p = nibble_to_high(syn_nib) ^ ((d & 1) ? kHigh : 0u);
+    for (int k = 0; k < d; ++k) p ^= E_s[(col[k] * Z + wrap(r + sh[k], Z)) * W + w];
+    return p & kHigh;
+}
+
+}  // namespace ldpc_dev

@@ -128,6 +128,45 @@ class QCCode:
         return bits, iters, ok
 
 
+    def reserve_persistent(self, list_len: int, words: int = 0, ctas_per_sm: int = 0) -> None:
+        with torch.cuda.device(self.device):
+            native.ldpc_code_reserve_persistent(self.handle, int(list_len), int(words), int(ctas_per_sm))
+
+    def reconcile_persistent(self, bob_bits, qber, syndrome, max_iter: int, rank=None, n_short=None, n_punct=None,
+                             known=None, frame_list=None, llr_scale: float = 8.0, words: int = 0,
+                             ctas_per_sm: int = 0, out=None):
+        """Fused LLR quantisation + layered decoding in one persistent launch
+        (frames indexed by id; ``frame_list`` selects which to decode).
+        Returns ``(bits, iters, ok)`` indexed by frame id."""
+        B = bob_bits.shape[0]
+        _dev_ptr(bob_bits, "bob_bits", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(qber, "qber", torch.float64, self.device, (B,))
+        _dev_ptr(syndrome, "syndrome", torch.uint8, self.device, (B, self.mbytes))
+        rp = _dev_ptr(rank, "rank", torch.int32, self.device, (self.n,))
+        sp = _dev_ptr(n_short, "n_short", torch.int32, self.device, (B,))
+        pp = _dev_ptr(n_punct, "n_punct", torch.int32, self.device, (B,))
+        kp = _dev_ptr(known, "known", torch.uint8, self.device, (B, self.nbytes))
+        if frame_list is not None:
+            lp = _dev_ptr(frame_list, "frame_list", torch.int32, self.device)
+            nl = int(frame_list.numel())
+        else:
+            lp, nl = None, B
+        if out is None:
+            out = (torch.zeros((B, self.nbytes), dtype=torch.uint8, device=self.device),
+                   torch.zeros((B,), dtype=torch.int32, device=self.device),
+                   torch.zeros((B,), dtype=torch.uint8, device=self.device))
+        bits, iters, ok = out
+        _dev_ptr(bits, "out bits", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(iters, "out iters", torch.int32, self.device, (B,))
+        _dev_ptr(ok, "out ok", torch.uint8, self.device, (B,))
+        with torch.cuda.device(self.device):
+            native.ldpc_reconcile_persistent(self.handle, bob_bits.data_ptr(), qber.data_ptr(), rp, sp, pp, kp,
+                                             syndrome.data_ptr(), B, lp, nl, int(max_iter), float(llr_scale),
+                                             int(words), int(ctas_per_sm), bits.data_ptr(), iters.data_ptr(),
+                                             ok.data_ptr(), self._stream())
+        return bits, iters, ok
+
+
 def tau_table_device(device=None) -> torch.Tensor:
     """The decoder's byte-lane tau evaluated on the GPU for all (p, q) < 128."""
     device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)

@@ -40,6 +40,8 @@ SIGNATURES = {
     "ldpc_decode_batch": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "ldpc_decode_batch_ex": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P, _P]),
     "ldpc_decode_batch_words": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P]),
+    "ldpc_reconcile_persistent": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _D, _I, _I, _P, _P, _P, _P]),
+    "ldpc_code_reserve_persistent": (_I, [_P, _I, _I, _I]),
     "ldpc_debug_tau_table": (_I, [_P, _P]),
     "ldpc_launch_count": (_I64, []),
     "ldpc_strerror": (ctypes.c_char_p, [_I]),
@@ -130,6 +132,17 @@ def ldpc_decode_batch_words(code, llr_in, target_syndrome, batch, max_iter, word
                             stream):
     _call("ldpc_decode_batch_words", code, llr_in, target_syndrome, batch, max_iter, words, out_bits, out_iters,
           out_ok, stream)
+
+
+def ldpc_reconcile_persistent(code, bob_bits, qber, rank, n_short, n_punct, known, target_syndrome, batch,
+                              frame_list, list_len, max_iter, llr_scale, words, ctas_per_sm, out_bits, out_iters,
+                              out_ok, stream):
+    _call("ldpc_reconcile_persistent", code, bob_bits, qber, rank, n_short, n_punct, known, target_syndrome, batch,
+          frame_list, list_len, max_iter, llr_scale, words, ctas_per_sm, out_bits, out_iters, out_ok, stream)
+
+
+def ldpc_code_reserve_persistent(code, list_len, words, ctas_per_sm):
+    _call("ldpc_code_reserve_persistent", code, list_len, words, ctas_per_sm)
 
 
 def ldpc_debug_tau_table(out, stream):

@@ -149,7 +149,7 @@ def test_decode_degree_zero_and_one_rows_and_high_degree():
     # row 1 stays empty (degree 0)
     base[2, :] = g.integers(0, Z, 40)    # degree 40 (64-edge kernel path)
     base[3, ::2] = g.integers(0, Z, 20)
-    base[4, 1::3] = g.integers(0, Z, 14)
+    base[4, 1::3] = g.integers(0, Z, len(range(1, 40, 3)))
     xa, yb = _frames(base, Z, 13, 0.03, 77)
     llr, syn_u = _oracle_inputs(base, Z, xa, yb, 0.03)
     gg, o = _decode_both(base, Z, llr, syn_u, 15)
