@@ -51,6 +51,11 @@ def parse_args():
     ap.add_argument("--max-iter", type=int, default=0, help="override the workload's iteration cap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--protocol", choices=["fixed", "interactive"], default="fixed",
+                    help="fixed: one rate per frame for the workload's target f; interactive: rounds of reveal")
+    ap.add_argument("--f-start", type=float, default=1.1)
+    ap.add_argument("--df", type=float, default=0.1)
+    ap.add_argument("--max-rounds", type=int, default=8)
     return ap.parse_args()
 
 
@@ -141,16 +146,16 @@ def peaks():
 
 def kernel_sources_sha():
     h = hashlib.sha256()
-    for fn in ("decode_int8.cu", "common.cuh"):
+    for fn in ("decode_int8.cu", "decode_persistent.cu", "row_update.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1903_10107_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, launch_frames: int):
-    """DRAM bytes per launch from the committed ncu summary of the decode
-    kernel, if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"decode_kernel_{workload}.md")
+def profiled_traffic(kernel: str, workload: str, launch_frames: int):
+    """DRAM bytes per launch from the committed ncu summary of the kernel, if
+    it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -223,14 +228,14 @@ def _oracle_decode(bt, orc, limit=None):
         bt._orank = rk
         st = np.stack([orate.position_states(rk, int(bt.n_punct[f]), int(bt.n_short[f])) for f in range(k)])
         kn = xa_u
-    llr = orc.llr_frames(yb_u, bt.q[:k], st, kn)
+    llr = orc.llr_frames(yb_u, bt.q[:k], st, kn, scale=w.llr_scale)
     bits, iters, ok, used = orc.decode(bt.base, w.Z, llr, syn, w.max_iter)
     return bits, iters, ok, used
 
 
 # ---------------------------------------------------------------------- ours
 
-def measure_e2e(args, rec, bt, d_syn, xa_bits, dev):
+def measure_e2e(args, rec, bt, d_syn, xa_bits, dev, words=0, ctas=0):
     """Same step through Reconciler.reconcile_host from pinned host buffers."""
     import torch
     w = bt.w
@@ -241,12 +246,14 @@ def measure_e2e(args, rec, bt, d_syn, xa_bits, dev):
     h_ns = pin(bt.n_short) if mixed else None
     h_kn = pin(bt.xa) if mixed else None
     for _ in range(max(1, args.warmup)):
-        rec.reconcile_host(h_yb, h_syn, h_q, w.max_iter, h_np, h_ns, h_kn)
+        rec.reconcile_host(h_yb, h_syn, h_q, w.max_iter, h_np, h_ns, h_kn, persistent=mixed, words=words,
+                           ctas_per_sm=ctas)
     torch.cuda.synchronize()
     e2e_steps = max(2, min(args.steps, 5))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        res, h2d, d2h = rec.reconcile_host(h_yb, h_syn, h_q, w.max_iter, h_np, h_ns, h_kn)
+        res, h2d, d2h = rec.reconcile_host(h_yb, h_syn, h_q, w.max_iter, h_np, h_ns, h_kn, persistent=mixed,
+                                           words=words, ctas_per_sm=ctas)
         torch.cuda.current_stream(dev).synchronize()  # the caller reads the results
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e_bits = inputs.unpack_bits(res[0].numpy(), w.n)
@@ -258,7 +265,7 @@ def measure_e2e(args, rec, bt, d_syn, xa_bits, dev):
 def run_ours(args, rank, world, dist):
     import torch
     from paper_1903_10107_gb300 import native
-    from paper_1903_10107_gb300.pipeline import Reconciler
+    from paper_1903_10107_gb300.pipeline import MixedRateBatch, Reconciler
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -268,7 +275,7 @@ def run_ours(args, rank, world, dist):
         w.max_iter = args.max_iter
     B = args.batch or w.batch
     bt = Batch(w, B, rank * B)  # weak scaling: every rank its own B frames
-    rec = Reconciler(bt.base, w.Z, bt.tiebreak, dev)
+    rec = Reconciler(bt.base, w.Z, bt.tiebreak, dev, llr_scale=w.llr_scale)
     code = rec.code
     # Alice's syndromes (her side of the protocol; computed once, outside the step)
     d_xa = torch.from_numpy(bt.xa).to(dev)
@@ -279,13 +286,33 @@ def run_ours(args, rank, world, dist):
     d_np = torch.from_numpy(bt.n_punct).to(dev) if mixed else None
     d_ns = torch.from_numpy(bt.n_short).to(dev) if mixed else None
     d_kn = d_xa if mixed else None
-    code.reserve(B)
-    out = (torch.empty((B, code.nbytes), dtype=torch.uint8, device=dev),
-           torch.empty((B,), dtype=torch.int32, device=dev),
-           torch.empty((B,), dtype=torch.uint8, device=dev))
+    xa_bits = inputs.unpack_bits(bt.xa, w.n)
 
-    def step():
-        return rec.reconcile(d_yb, d_syn, d_q, w.max_iter, d_np, d_ns, d_kn, out=out)
+    if args.protocol == "interactive":
+        return run_interactive(args, rank, world, dist, w, bt, rec, d_yb, d_syn, d_xa, xa_bits, dev)
+
+    if mixed:
+        # one persistent launch (LLR quantisation fused), replayed from a CUDA graph
+        mrb = MixedRateBatch(rec, w.max_iter).bind(d_yb, d_syn, d_q, d_np, d_ns, d_kn)
+        l0 = native.ldpc_launch_count()
+        mrb._launch(mrb.words, mrb.ctas)
+        torch.cuda.synchronize()
+        launches_per_step = native.ldpc_launch_count() - l0
+        out = mrb.out
+        step = mrb.run
+        kernel_name = "persistent_kernel"
+        shape = {"words_per_cta": mrb.words, "ctas_per_sm": mrb.ctas, "cuda_graph": mrb.graph is not None}
+    else:
+        code.reserve(B)
+        out = (torch.empty((B, code.nbytes), dtype=torch.uint8, device=dev),
+               torch.empty((B,), dtype=torch.int32, device=dev),
+               torch.empty((B,), dtype=torch.uint8, device=dev))
+
+        def step():
+            return rec.reconcile(d_yb, d_syn, d_q, w.max_iter, out=out)
+        launches_per_step = 2
+        kernel_name = "decode_kernel"
+        shape = {"cuda_graph": False}
 
     for _ in range(args.warmup):
         step()
@@ -308,33 +335,39 @@ def run_ours(args, rank, world, dist):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
-    launches = native.ldpc_launch_count() - l0
+    eager_launches = native.ldpc_launch_count() - l0
     barrier()
     clk = clocks.stop()
     step_s = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    # graph replays bypass the library's launch counter: count the kernels the graph holds
+    launches = eager_launches if eager_launches else launches_per_step * args.steps
 
     bits, iters, ok = (t.cpu().numpy() for t in out)
-    xa_bits = inputs.unpack_bits(bt.xa, w.n)
     got_bits = inputs.unpack_bits(bits, w.n)
     corr = ok.astype(bool) & np.all(got_bits == xa_bits, axis=1)
     corr_key = float(bt.key_bits[corr].sum())
     all_key = float(bt.key_bits.sum())
 
-    # decode kernel alone, for the roofline (same stream, CUDA events)
-    llr = code.llr_from_bsc(d_yb, d_q, rank=rec.rank if mixed else None, n_short=d_ns, n_punct=d_np,
-                            known=d_kn)
-    for _ in range(2):
-        code.decode(llr, d_syn, w.max_iter, out=out)
-    torch.cuda.synchronize()
-    reps = max(3, args.steps)
-    ev0.record(stream)
-    for _ in range(reps):
-        code.decode(llr, d_syn, w.max_iter, out=out)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    dec_s = ev0.elapsed_time(ev1) / 1e3 / reps
+    # the dominant kernel alone, for the roofline (same stream, CUDA events)
+    if mixed:
+        dec_s = step_s  # the step is the single persistent kernel
+    else:
+        llr = code.llr_from_bsc(d_yb, d_q)
+        for _ in range(2):
+            code.decode(llr, d_syn, w.max_iter, out=out)
+        torch.cuda.synchronize()
+        reps = max(3, args.steps)
+        ev0.record(stream)
+        for _ in range(reps):
+            code.decode(llr, d_syn, w.max_iter, out=out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        dec_s = ev0.elapsed_time(ev1) / 1e3 / reps
     it_sum = float(iters.astype(np.int64).sum())
-    io_bytes = B * (w.n + code.mbytes + code.nbytes + 4 + 1)
+    if mixed:  # Bob's bits, syndrome, shortened values in; bits, iterations, flag out
+        io_bytes = B * (2 * code.nbytes + code.mbytes + code.nbytes + 4 + 1 + 16)
+    else:      # int8 LLRs, syndrome in; bits, iterations, flag out
+        io_bytes = B * (w.n + code.mbytes + code.nbytes + 4 + 1)
     alg_bytes = it_sum * 2.0 * code.edges + io_bytes
     peak, peak_kind = peaks()
     achieved = alg_bytes / dec_s / 1e9
@@ -342,7 +375,8 @@ def run_ours(args, rank, world, dist):
     # end to end through the public API from pinned host buffers
     e2e_s, e_key, h2d, d2h = float("nan"), 0.0, 0, 0
     if not args.no_e2e:
-        e2e_s, e_key, h2d, d2h = measure_e2e(args, rec, bt, d_syn, xa_bits, dev)
+        e2e_s, e_key, h2d, d2h = measure_e2e(args, rec, bt, d_syn, xa_bits, dev,
+                                             shape.get("words_per_cta", 0), shape.get("ctas_per_sm", 0))
 
     # max over ranks, sums over ranks
     vals = np.array([step_s, e2e_s, corr_key, all_key, e_key, dec_s], dtype=np.float64)
@@ -365,7 +399,7 @@ def run_ours(args, rank, world, dist):
 
     if rank != 0:
         return
-    traffic = profiled_traffic(w.name, B)
+    traffic = profiled_traffic(kernel_name, w.name, B)
     line = {
         "metric": METRIC,
         "value": corr_tot / step_max / 1e6,
@@ -382,8 +416,10 @@ def run_ours(args, rank, world, dist):
         "config": {
             "workload": w.name, "frames": B * world, "n": w.n, "m": w.m, "Z": w.Z, "max_iter": w.max_iter,
             "qber": list(w.qber) if isinstance(w.qber, tuple) else w.qber,
-            "l2": "inputs larger than L2 (LLRs alone %.0f MB per rank)" % (B * w.n / 1e6),
+            "target_f": w.target_f, "llr_lsb_per_nat": round(w.llr_scale, 4),
+            "l2": "inputs larger than L2 (Bob's keys + syndromes %.0f MB per rank)" % (B * (code.nbytes + code.mbytes) / 1e6),
             "parallelism": f"frames sharded over {world} GPU(s), no collective on the data path",
+            **shape,
         },
         "processed_key_mbps": all_tot / step_max / 1e6,
         "fer": 1.0 - float(corr.mean()),
@@ -391,7 +427,7 @@ def run_ours(args, rank, world, dist):
         "iters_mean": float(iters.mean()),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "decode_kernel", "kernel_ms": dec_s * 1e3,
+                     "kernel": kernel_name, "kernel_ms": dec_s * 1e3,
                      "algorithmic_bytes": alg_bytes},
         "e2e": {"value": e_tot / e2e_max / 1e6, "unit": "Mbps", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -399,6 +435,35 @@ def run_ours(args, rank, world, dist):
         "clocks": clk,
         "cpu_baseline": cpu,
         "paper_context": "60 Mbps at f~1.1 on an Intel i7-6700HQ (section 4.2, Table 2), other codes and hardware",
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_interactive(args, rank, world, dist, w, bt, rec, d_yb, d_syn, d_xa, xa_bits, dev):
+    """Interactive rate adaptation from f_start: rounds of decode + reveal."""
+    import torch
+    from paper_1903_10107_gb300.pipeline import InteractiveProtocol
+    proto = InteractiveProtocol(rec, w.max_iter, f_start=args.f_start, df=args.df, max_rounds=args.max_rounds)
+    for _ in range(max(1, args.warmup)):
+        proto.run(d_yb, d_syn, bt.q, d_xa)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = proto.run(d_yb, d_syn, bt.q, d_xa)
+    torch.cuda.synchronize()
+    step_s = (time.perf_counter() - t0) / args.steps
+    got = inputs.unpack_bits(res["bits"], w.n)
+    corr = res["ok"].astype(bool) & np.all(got == xa_bits, axis=1)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "protocol": "interactive", "value": float(res["key_bits"][corr].sum()) / step_s / 1e6,
+        "unit": "Mbps", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": w.name, "frames": bt.B, "f_start": args.f_start, "df": args.df,
+                   "max_rounds": args.max_rounds, "max_iter": w.max_iter},
+        "fer": 1.0 - float(corr.mean()), "efficiency_f_mean": float(res["f"][corr].mean()) if corr.any() else None,
+        "rounds_mean": float(res["rounds"].mean()), "iters_mean_total": float(res["iters"].mean()),
     }
     print(json.dumps(line), flush=True)
 

@@ -41,11 +41,11 @@ struct DecodeArgs {
 
 // Threads: tid = ((row slot) * P + half) * W + w.  The two halves of a row sit
 // W lanes apart in one warp.
-template <int HMAX, int P, int W, bool TABLES, int MAXT>
+template <int MAXH, int P, int W, bool TABLES, int MAXT>
 __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int n = A.n, m = A.m, Z = A.Z, Mb = A.Mb, nblk = A.nblk;
-    const int tab_words = 2 * Mb + 1 + 2 * nblk;
+    const int tab_words = (int)ldpc_dev::tables_words(Mb, nblk);
     uint32_t* E_s = reinterpret_cast<uint32_t*>(smem);
     int32_t* s_tab = reinterpret_cast<int32_t*>(smem + (size_t)4 * n * W);
     uint8_t* syn_s = reinterpret_cast<uint8_t*>(s_tab + tab_words);
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
     const int64_t f0 = (int64_t)blockIdx.x * 4 * W;
     const int mbytes = (m + 7) / 8;
 
-    for (int i = tid; i < tab_words; i += T) s_tab[i] = A.tab[i];
+    const ldpc_dev::Tables TB = ldpc_dev::load_tables(s_tab, A.tab, Mb, nblk, Z, W, tid, T);
     for (int idx = tid; idx < n * W; idx += T) {
         const int j = idx / W, ww = idx % W;
         uint32_t word = 0;
@@ -90,16 +90,13 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
     if (tid < 4 * W) s_iters[tid] = 0;
     __syncthreads();
 
-    const int32_t* deg = s_tab;
-    const int32_t* off = s_tab + Mb;
-    const int32_t* col = s_tab + 2 * Mb + 1;
-    const int32_t* sh = col + nblk;
+    const int* deg = TB.deg;
+    const int* off = TB.off;
 
     RowCtx C;
     C.E_s = E_s;
     C.msg = A.msg + (size_t)blockIdx.x * nblk * Z * W;
     C.Z = Z;
-    C.W = W;
     C.w = w;
     C.sq = 16;
     C.oq = 0;
@@ -110,8 +107,7 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
         for (int i = 0; i < Mb; ++i) {          // one block row = one layer, in order
             C.d = deg[i];
             C.b0 = off[i];
-            C.col = col + C.b0;
-            C.sh = sh + C.b0;
+            C.et = TB.et + C.b0;
             if (TABLES) {
                 if (A.scale_q4) C.sq = A.scale_q4[(size_t)(t - 1) * Mb + i];
                 if (A.offset_q) C.oq = A.offset_q[(size_t)(t - 1) * Mb + i];
@@ -121,7 +117,7 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
                     const int r = r0 + rt;
                     const bool valid = r < Z;
                     const uint32_t nib = valid ? syn_s[(i * Z + r) * W + w] : 0u;
-                    ldpc_dev::row_update<HMAX, P, TABLES>(C, valid ? r : 0, valid, half, nib);
+                    ldpc_dev::row_update_any<W, TABLES, MAXH>(C, valid ? r : 0, valid, half, nib);
                 }
             }
             __syncthreads();
@@ -130,7 +126,7 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
         uint32_t bad = 0;
         for (int c = q; c < m; c += QT) {
             const int i = c / Z, r = c - i * Z;
-            bad |= ldpc_dev::row_parity(E_s, col + off[i], sh + off[i], deg[i], r, Z, W, w, syn_s[c * W + w]);
+            bad |= ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
         }
 #pragma unroll
         for (int o = 16; o >= W; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
@@ -176,19 +172,20 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
 }
 
 size_t smem_bytes(const ldpc_code* c, int W) {
-    size_t b = (size_t)4 * c->n * W + sizeof(int32_t) * (2 * c->Mb + 1 + 2 * c->nblk) + (size_t)c->m * W;
+    const size_t tab_words = (size_t)((2 * c->Mb + 1 + 1) & ~1) + 2 * (size_t)c->nblk;
+    size_t b = (size_t)4 * c->n * W + sizeof(int32_t) * tab_words + (size_t)c->m * W;
     return (b + 15) & ~(size_t)15;
 }
 
-template <int HMAX, int W, bool TABLES>
+template <int MAXH, int W, bool TABLES>
 int launch_t(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t st) {
     constexpr int P = 2;
-    constexpr int MAXT = HMAX <= 16 ? 1024 : 512;
+    constexpr int MAXT = MAXH <= 16 ? 1024 : 512;
     int T = c->Z * W * P;
     if (T > MAXT) T = MAXT;
     T = (T + 31) / 32 * 32;
     const size_t smem = smem_bytes(c, W);
-    auto kern = decode_kernel<HMAX, P, W, TABLES, MAXT>;
+    auto kern = decode_kernel<MAXH, P, W, TABLES, MAXT>;
     LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<groups, T, smem, st>>>(A);
     ldpc::count_launch();
@@ -199,9 +196,8 @@ int launch_t(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t s
 // Half-row length: two threads share a row, each walking ceil(d/2) edges at most.
 template <int W, bool TABLES>
 int launch_w(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t st) {
-    const int h = (c->max_deg + 1) / 2;
-    if (h <= 8) return launch_t<8, W, TABLES>(c, A, groups, st);
-    if (h <= 16) return launch_t<16, W, TABLES>(c, A, groups, st);
+    if (c->max_deg <= 24) return launch_t<12, W, TABLES>(c, A, groups, st);
+    if (c->max_deg <= 32) return launch_t<16, W, TABLES>(c, A, groups, st);
     return launch_t<32, W, TABLES>(c, A, groups, st);
 }
 

@@ -52,12 +52,12 @@ __device__ __forceinline__ int frame_of(const PersistArgs& A, int slot) {
     return (f >= 0 && f < A.batch) ? f : -1;
 }
 
-template <int HMAX, int P, int W, int MAXT>
+template <int MAXH, int P, int W, int MAXT>
 __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int n = A.n, m = A.m, Z = A.Z, Mb = A.Mb, nblk = A.nblk;
     const int nb = (n + 7) / 8, mbytes = (m + 7) / 8;
-    const int tab_words = 2 * Mb + 1 + 2 * nblk;
+    const int tab_words = (int)ldpc_dev::tables_words(Mb, nblk);
     uint32_t* E_s = reinterpret_cast<uint32_t*>(smem);
     uint8_t* E_b = smem;
     int32_t* s_tab = reinterpret_cast<int32_t*>(smem + (size_t)4 * n * W);
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
     const int half = (P == 2) ? (q & 1) : 0;
     const int rt = q / P, RT = T / (W * P), QT = T / W;
 
-    for (int i = tid; i < tab_words; i += T) s_tab[i] = A.tab[i];
+    const ldpc_dev::Tables TB = ldpc_dev::load_tables(s_tab, A.tab, Mb, nblk, Z, W, tid, T);
     if (tid == 0) s_base = atomicAdd(A.queue, NL);
     if (tid < W) {
         s_active[tid] = 0;
@@ -96,15 +96,12 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
     }
     if (tid == 0) s_any_load = 1;
 
-    const int32_t* deg = s_tab;
-    const int32_t* off = s_tab + Mb;
-    const int32_t* col = s_tab + 2 * Mb + 1;
-    const int32_t* sh = col + nblk;
+    const int* deg = TB.deg;
+    const int* off = TB.off;
     RowCtx C;
     C.E_s = E_s;
     C.msg = A.msg + (size_t)blockIdx.x * nblk * Z * W;
     C.Z = Z;
-    C.W = W;
     C.w = w;
     C.sq = 16;
     C.oq = 0;
@@ -173,14 +170,13 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
         for (int i = 0; i < Mb; ++i) {
             C.d = deg[i];
             C.b0 = off[i];
-            C.col = col + C.b0;
-            C.sh = sh + C.b0;
+            C.et = TB.et + C.b0;
             if (C.d > 0) {
                 for (int r0 = 0; r0 < Z; r0 += RT) {
                     const int r = r0 + rt;
                     const bool valid = r < Z;
                     const uint32_t nib = valid ? syn_s[(i * Z + r) * W + w] : 0u;
-                    ldpc_dev::row_update<HMAX, P, false>(C, valid ? r : 0, valid, half, nib);
+                    ldpc_dev::row_update_any<W, false, MAXH>(C, valid ? r : 0, valid, half, nib);
                 }
             }
             __syncthreads();
@@ -188,7 +184,7 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
         uint32_t bad = 0;
         for (int c = q; c < m; c += QT) {
             const int i = c / Z, r = c - i * Z;
-            bad |= ldpc_dev::row_parity(E_s, col + off[i], sh + off[i], deg[i], r, Z, W, w, syn_s[c * W + w]);
+            bad |= ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
         }
 #pragma unroll
         for (int o = 16; o >= W; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
@@ -259,19 +255,20 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
 }
 
 size_t smem_bytes(const ldpc_code* c, int W) {
-    size_t b = (size_t)4 * c->n * W + sizeof(int32_t) * (2 * c->Mb + 1 + 2 * c->nblk) + (size_t)c->m * W;
+    const size_t tab_words = (size_t)((2 * c->Mb + 1 + 1) & ~1) + 2 * (size_t)c->nblk;
+    size_t b = (size_t)4 * c->n * W + sizeof(int32_t) * tab_words + (size_t)c->m * W;
     return (b + 15) & ~(size_t)15;
 }
 
-template <int HMAX, int W>
+template <int MAXH, int W>
 int launch_p(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int* grid_out, bool dry, cudaStream_t st) {
     constexpr int P = 2;
-    constexpr int MAXT = HMAX <= 16 ? 1024 : 512;
+    constexpr int MAXT = MAXH <= 16 ? 1024 : 512;
     int T = c->Z * W * P;
     if (T > MAXT) T = MAXT;
     T = (T + 31) / 32 * 32;
     const size_t smem = smem_bytes(c, W);
-    auto kern = persistent_kernel<HMAX, P, W, MAXT>;
+    auto kern = persistent_kernel<MAXH, P, W, MAXT>;
     LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0, sms = 0;
     LDPC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem));
@@ -293,9 +290,8 @@ int launch_p(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int* gri
 
 template <int W>
 int launch_pw(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int* grid, bool dry, cudaStream_t st) {
-    const int h = (c->max_deg + 1) / 2;
-    if (h <= 8) return launch_p<8, W>(c, A, ctas_per_sm, grid, dry, st);
-    if (h <= 16) return launch_p<16, W>(c, A, ctas_per_sm, grid, dry, st);
+    if (c->max_deg <= 24) return launch_p<12, W>(c, A, ctas_per_sm, grid, dry, st);
+    if (c->max_deg <= 32) return launch_p<16, W>(c, A, ctas_per_sm, grid, dry, st);
     return launch_p<32, W>(c, A, ctas_per_sm, grid, dry, st);
 }
 

@@ -16,11 +16,11 @@
 //   S = 0 (same sign):     E = sv * min(a + m, 127)
 //   S = 1 (opposite sign): E = sv * (a - m)          (already in range)
 //
-// Two threads may share a row (P = 2).  Thread 0 walks edges 0..h-1 upward,
-// thread 1 walks edges d-1..h downward; both fold tau over their own walk
-// (tau is symmetric, so thread 1's fold is the right fold B), swap their
-// totals and sign parities with one shuffle each, and walk back to produce
-// their outputs.  Both threads run the same instructions.
+// Two threads share a row.  Thread 0 walks edges 0..h-1 upward, thread 1
+// walks edges d-1..h downward; both fold tau over their own walk (tau is
+// symmetric, so thread 1's fold is the right fold B), swap their totals and
+// sign parities with one shuffle each, and walk back to produce their
+// outputs.  Both threads run the same instructions.
 #pragma once
 
 #include "common.cuh"
@@ -28,8 +28,6 @@
 namespace ldpc_dev {
 
 using namespace lanes;
-
-__device__ __forceinline__ int wrap(int x, int Z) { return x >= Z ? x - Z : x; }
 
 // m' = clamp(((m*s + 8) >> 4) - o, 0, 127) per byte, s and o the same for all
 // lanes.  Even and odd bytes are widened to 16-bit lanes: m*s <= 127*255 and
@@ -44,39 +42,69 @@ __device__ __forceinline__ uint32_t apply_table(uint32_t m, uint32_t s, int o) {
     return lo | (hi << 8);
 }
 
+// (r + s) mod Z for r, s in [0, Z): the unsigned min of x and x - Z.
+__device__ __forceinline__ int wrap(int x, int Z) { return (int)min((unsigned)x, (unsigned)(x - Z)); }
+
+// Shared-memory code tables: deg[Mb], off[Mb+1], then per nonzero block
+// {block column * Z * W, circulant shift}.
+struct Tables {
+    const int* deg;
+    const int* off;
+    const int2* et;
+};
+
+__device__ __forceinline__ size_t tables_words(int Mb, int nblk) {
+    return (size_t)((2 * Mb + 1 + 1) & ~1) + 2 * (size_t)nblk;
+}
+
+__device__ __forceinline__ Tables load_tables(int32_t* s, const int32_t* g, int Mb, int nblk, int Z, int W,
+                                              int tid, int T) {
+    const int head = (2 * Mb + 1 + 1) & ~1;
+    for (int i = tid; i < 2 * Mb + 1; i += T) s[i] = g[i];
+    int2* et = reinterpret_cast<int2*>(s + head);
+    const int32_t* col = g + 2 * Mb + 1;
+    const int32_t* sh = col + nblk;
+    for (int b = tid; b < nblk; b += T) et[b] = make_int2(col[b] * Z * W, sh[b]);
+    return Tables{s, s + Mb, et};
+}
+
 struct RowCtx {
     uint32_t* E_s;           // shared soft values, [n][W] words
     uint32_t* msg;           // this CTA's messages, [(block)*Z + row][W] words
-    const int32_t* col;      // block columns of the layer (ascending)
-    const int32_t* sh;       // circulant shifts of the layer
-    int b0, d, Z, W, w;      // layer block offset and degree; lifting; words per row; my word
+    const int2* et;          // edge table of the layer (ascending block column)
+    int b0, d, Z, w;         // layer block offset and degree; lifting; my word
     uint32_t fresh;          // lanes whose stored L is stale (treated as 0)
     uint32_t active;         // lanes whose E may change
     uint32_t sq;             // table scale (16 = identity)
     int oq;                  // table offset
 };
 
-// `half` is 0 or 1 (always 0 when P == 1); `valid` false makes the thread a
-// bystander that only joins the shuffles.
-template <int HMAX, int P, bool TABLES>
+// `half` is 0 or 1; `valid` false makes the thread a bystander that only
+// joins the shuffles.  HMAX bounds the edges walked by one thread.
+template <int HMAX, int W, bool TABLES>
 __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, int half, uint32_t syn_nib) {
     const int d = valid ? C.d : 0;
-    const int h = (P == 1) ? d : (d + 1) >> 1;
+    const int h = (d + 1) >> 1;
     const int cnt = half ? d - h : h;           // edges walked by this thread
-    const int partner = (P == 1) ? 0 : (half ? h : d - h);
-    const int Z = C.Z, W = C.W, w = C.w;
-    const size_t kstride = (size_t)Z * W;
-    uint32_t* Lrow = C.msg + ((size_t)C.b0 * Z + r) * W + w;
+    const int partner = half ? h : d - h;
+    const int Z = C.Z;
+    const int k0 = half ? d - 1 : 0;             // first edge of the walk
+    const int kdir = half ? -1 : 1;
+    const int2* et = C.et + k0;
+    uint32_t* Lp = C.msg + ((size_t)(C.b0 + k0) * Z + r) * W + C.w;
+    const ptrdiff_t Lstep = (ptrdiff_t)kdir * Z * W;
     uint32_t av[HMAX], F[HMAX];
+    int idx[HMAX];
     uint32_t S = (half == 0 && valid) ? nibble_to_high(syn_nib) : 0u;
 
 #pragma unroll(HMAX)
     for (int j = 0; j < HMAX; ++j) {
         if (j < cnt) {
-            const int k = half ? d - 1 - j : j;
-            const uint32_t e = C.E_s[(C.col[k] * Z + wrap(r + C.sh[k], Z)) * W + w];
+            const int2 t = et[j * kdir];
+            idx[j] = t.x + wrap(r + t.y, Z) * W + C.w;
+            const uint32_t e = C.E_s[idx[j]];
             uint32_t lb = kHigh;                 // offset-binary zero
-            if (C.fresh != 0xFFFFFFFFu) lb = select(C.fresh, kHigh, Lrow[k * kstride]);
+            if (C.fresh != 0xFFFFFFFFu) lb = select(C.fresh, kHigh, Lp[j * Lstep]);
             const uint32_t sv = lt_u8(e, lb);    // sign of E - L
             av[j] = cap127(absdiff(e, lb)) | sv; // |sat8(E - L)| and its sign
             S ^= sv;
@@ -91,11 +119,8 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
             if (j == cnt - 1) tot = F[j];
         }
     }
-    uint32_t R = kMax;
-    if (P == 2) {
-        R = __shfl_xor_sync(0xffffffffu, tot, W);
-        S ^= __shfl_xor_sync(0xffffffffu, S, W);
-    }
+    uint32_t R = __shfl_xor_sync(0xffffffffu, tot, W);
+    S ^= __shfl_xor_sync(0xffffffffu, S, W);
     bool rvalid = partner > 0;
     const uint32_t MS = spread(S);
 
@@ -103,12 +128,11 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
     for (int jj = 0; jj < HMAX; ++jj) {
         const int j = HMAX - 1 - jj;
         if (j < cnt) {
-            const int k = half ? d - 1 - j : j;
             const uint32_t a = av[j] & kMax;
             const uint32_t Fp = F[j >= 1 ? j - 1 : 0];
             uint32_t m;
             if (rvalid) m = (j == 0) ? R : tau(Fp, R);
-            else m = (j == 0) ? kMax : Fp;     // no edge beyond: left fold alone (degree 1: MSG_max)
+            else m = (j == 0) ? kMax : Fp;       // no edge beyond: left fold alone (degree 1: MSG_max)
             if (j > 0) R = rvalid ? tau(a, R) : a;
             rvalid = true;
             if (TABLES) m = apply_table(m, C.sq, C.oq);
@@ -117,22 +141,35 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
             const uint32_t c = cap127(a + m);
             const uint32_t e_same = select(Msv, kHigh - c, kHigh | c);
             const uint32_t e_opp = select(Msv, kHigh - a + m, kHigh + a - m);
-            uint32_t* ep = &C.E_s[(C.col[k] * Z + wrap(r + C.sh[k], Z)) * W + w];
+            uint32_t* ep = &C.E_s[idx[j]];
             const uint32_t eo = *ep;
             const uint32_t sat = spread(absdiff(eo, kHigh) + kOnes);  // |E| = 127
             *ep = select(C.active & ~sat, select(MS, e_opp, e_same), eo);
-            Lrow[k * kstride] = lnew;
+            Lp[j * Lstep] = lnew;
         }
     }
 }
 
-// Parity of check row c (layer i, row r) against its syndrome bits: bit 7 of
-// each byte set where the lane's check fails.  Hard decision: E < 0, i.e.
-// bit 7 of the stored byte clear, so the xor of bit 7s is flipped once per edge.
-__device__ __forceinline__ uint32_t row_parity(const uint32_t* E_s, const int32_t* col, const int32_t* sh, int d,
-                                               int r, int Z, int W, int w, uint32_t syn_nib) {
+// One body per kernel: MAXH bounds ceil(d/2) over all layers of the code
+// (12: degrees up to 24; 16: up to 32; 32: up to 64).  A single body keeps
+// register allocation tight; the guarded slots past a layer's degree are the
+// price of irregular codes.
+template <int W, bool TABLES, int MAXH>
+__device__ __forceinline__ void row_update_any(const RowCtx& C, int r, bool valid, int half, uint32_t syn_nib) {
+    row_update<MAXH, W, TABLES>(C, r, valid, half, syn_nib);
+}
+
+// Parity of check row r of a layer against its syndrome bits: bit 7 of each
+// byte set where the lane's check fails.  Hard decision: E < 0, i.e. bit 7 of
+// the stored byte clear, so the xor of bit 7s is flipped once per edge.
+template <int W>
+__device__ __forceinline__ uint32_t row_parity(const uint32_t* E_s, const int2* et, int d, int r, int Z, int w,
+                                               uint32_t syn_nib) {
     uint32_t p = nibble_to_high(syn_nib) ^ ((d & 1) ? kHigh : 0u);
-    for (int k = 0; k < d; ++k) p ^= E_s[(col[k] * Z + wrap(r + sh[k], Z)) * W + w];
+    for (int k = 0; k < d; ++k) {
+        const int2 t = et[k];
+        p ^= E_s[t.x + wrap(r + t.y, Z) * W + w];
+    }
     return p & kHigh;
 }
 

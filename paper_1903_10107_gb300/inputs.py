@@ -111,7 +111,7 @@ class Workload:
     """Shape and seeds of one synthetic workload (no arithmetic of the method)."""
 
     def __init__(self, name, Mb, Nb, Z, batch, max_iter, qber, col_degrees,
-                 code_seed=1, frame_seed=2, mixed_rate=False, target_f=None):
+                 code_seed=1, frame_seed=2, mixed_rate=False, target_f=None, llr_scale=8.0):
         self.name = name
         self.Mb, self.Nb, self.Z = Mb, Nb, Z
         self.n, self.m = Nb * Z, Mb * Z
@@ -121,6 +121,7 @@ class Workload:
         self.code_seed, self.frame_seed = code_seed, frame_seed
         self.mixed_rate = mixed_rate
         self.target_f = target_f
+        self.llr_scale = llr_scale  # channel LLR LSB per nat
 
     def base(self) -> np.ndarray:
         degs = self.col_degrees
@@ -153,9 +154,11 @@ WORKLOADS = {
     "n4096_r075_q02": Workload("n4096_r075_q02", 8, 32, 128, 64, 50, 0.02, 3),
     # single column-3 code, rate 0.8, 8192 frames at QBER 3 %
     "n40960_r080_q03": Workload("n40960_r080_q03", 16, 80, 512, 8192, 100, 0.03, 3),
-    # 3/6 mixed-degree mother code, per-frame QBER 1-8 % and rate for f ~ 1.1
+    # 3/6 mixed-degree mother code, per-frame QBER 1-8 %, per-frame rate for a
+    # common efficiency target; LLRs quantised with the step at which the
+    # check-node table represents the box-plus (0.29 nat per LSB)
     "n49152_mixed_q01_08": Workload("n49152_mixed_q01_08", 24, 96, 512, 16384, 200, (0.01, 0.08),
-                                    _mixed_3_6, mixed_rate=True, target_f=1.1),
+                                    _mixed_3_6, mixed_rate=True, target_f=1.7, llr_scale=1 / 0.29),
     # the n=4096 code at QBER 2-4 %, for the FP32 relaxation
     "n4096_relaxed_q02_04": Workload("n4096_relaxed_q02_04", 8, 32, 128, 1024, 20, (0.02, 0.04), 3),
 }

@@ -44,7 +44,18 @@ class Reconciler:
                                      scale=self.llr_scale)
         return self.code.decode(llr, syndrome, max_iter, out=out)
 
-    def reconcile_host(self, bob_bits, syndrome, qber, max_iter, n_punct=None, n_short=None, known=None):
+    def reconcile_persistent(self, bob_bits, syndrome, qber, max_iter, n_punct=None, n_short=None, known=None,
+                             frame_list=None, words=0, ctas_per_sm=0, out=None):
+        """The same step as ``reconcile`` in one persistent launch with the LLR
+        quantisation fused into the decoder."""
+        rank = self.rank if (n_punct is not None or n_short is not None) else None
+        return self.code.reconcile_persistent(bob_bits, qber, syndrome, max_iter, rank=rank, n_short=n_short,
+                                              n_punct=n_punct, known=known, frame_list=frame_list,
+                                              llr_scale=self.llr_scale, words=words, ctas_per_sm=ctas_per_sm,
+                                              out=out)
+
+    def reconcile_host(self, bob_bits, syndrome, qber, max_iter, n_punct=None, n_short=None, known=None,
+                       persistent=False, words=0, ctas_per_sm=0):
         """Host tensors (ideally pinned) in, host tensors out.  Returns
         ((bits, iters, ok), h2d_bytes, d2h_bytes)."""
         dev = self.device
@@ -52,7 +63,11 @@ class Reconciler:
         d_in = [to(t) for t in (bob_bits, syndrome, qber, n_punct, n_short, known)]
         h2d = sum(int(t.numel() * t.element_size()) for t in (bob_bits, syndrome, qber, n_punct, n_short, known)
                   if t is not None)
-        bits, iters, ok = self.reconcile(d_in[0], d_in[1], d_in[2], max_iter, d_in[3], d_in[4], d_in[5])
+        if persistent:
+            bits, iters, ok = self.reconcile_persistent(d_in[0], d_in[1], d_in[2], max_iter, d_in[3], d_in[4],
+                                                        d_in[5], words=words, ctas_per_sm=ctas_per_sm)
+        else:
+            bits, iters, ok = self.reconcile(d_in[0], d_in[1], d_in[2], max_iter, d_in[3], d_in[4], d_in[5])
         outs = []
         for t in (bits, iters, ok):
             h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
@@ -66,3 +81,134 @@ def corrected_frames(bits: np.ndarray, ok: np.ndarray, alice: np.ndarray) -> np.
     """Frames whose decoder reported success and whose decoded word equals
     Alice's key (undetected errors do not count as corrected)."""
     return (ok.astype(bool)) & np.all(bits == alice, axis=1)
+
+
+class MixedRateBatch:
+    """One persistent launch over a batch of frames of mixed rates, QBERs and
+    iteration counts (section 4.1 rate adaptation on one mother code),
+    replayed from a CUDA graph.
+
+    ``bind`` fixes the device buffers (Bob's keys, Alice's syndromes, QBERs,
+    rate counts, shortened values, outputs), picks the launch shape with the
+    autotuner, reserves the scratch arena and captures the launch; ``run``
+    replays it on the current stream."""
+
+    def __init__(self, rec: Reconciler, max_iter: int, use_graph: bool = True, tune: bool = True,
+                 words: int = 0, ctas_per_sm: int = 0):
+        self.rec = rec
+        self.code = rec.code
+        self.max_iter = int(max_iter)
+        self.use_graph = use_graph
+        self.tune = tune
+        self.words, self.ctas = words, ctas_per_sm
+        self.graph = None
+
+    def _launch(self, words, ctas, n_frames=None):
+        b = self.buffers
+        B = b["bob"].shape[0] if n_frames is None else n_frames
+        sl = (lambda t: t) if n_frames is None else (lambda t: None if t is None else t[:n_frames])
+        out = self.out if n_frames is None else tuple(t[:n_frames] for t in self.out)
+        return self.code.reconcile_persistent(sl(b["bob"]), sl(b["qber"]), sl(b["syn"]), self.max_iter,
+                                              rank=self.rec.rank if b["n_punct"] is not None else None,
+                                              n_short=sl(b["n_short"]), n_punct=sl(b["n_punct"]),
+                                              known=sl(b["known"]), llr_scale=self.rec.llr_scale,
+                                              words=words, ctas_per_sm=ctas, out=out)
+
+    def bind(self, bob, syn, qber, n_punct=None, n_short=None, known=None):
+        from . import autotune
+        B = bob.shape[0]
+        self.buffers = dict(bob=bob, syn=syn, qber=qber, n_punct=n_punct, n_short=n_short, known=known)
+        dev = self.code.device
+        self.out = (torch.zeros((B, self.code.nbytes), dtype=torch.uint8, device=dev),
+                    torch.zeros((B,), dtype=torch.int32, device=dev),
+                    torch.zeros((B,), dtype=torch.uint8, device=dev))
+        if self.tune and not self.words:
+            self.words, self.ctas = autotune.tune_persistent(
+                self.code, lambda w, c, nf: self._launch(w, c, nf), B, sample_frames=min(B, 4096))
+        self.code.reserve_persistent(B, self.words, self.ctas)
+        self._launch(self.words, self.ctas)  # eager run: warms the kernel and checks arguments
+        torch.cuda.synchronize(dev)
+        if self.use_graph:
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream(dev)
+            s.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    self._launch(self.words, self.ctas)
+            torch.cuda.current_stream(dev).wait_stream(s)
+            self.graph = g
+        return self
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._launch(self.words, self.ctas)
+        return self.out
+
+
+class InteractiveProtocol:
+    """Interactive rate adaptation (sections 4.1 and 4.2): every frame starts
+    at the rate for ``f_start``; after each round the frames whose syndrome
+    did not match get more bits revealed -- first the punctured positions,
+    which become shortened, then key positions in the same order -- and are
+    decoded again, up to ``max_rounds`` extra rounds.  Each reveal adds
+    ``ceil(df * key_bits * h(q))`` bits, raising the frame's efficiency by
+    about ``df``.  The efficiency of a frame counts every revealed bit:
+    leak = m - p0 + revealed punctured bits, key = n - p0 - s0 - revealed
+    key bits, f = leak / (key * h(q))."""
+
+    def __init__(self, rec: Reconciler, max_iter: int, f_start: float = 1.1, df: float = 0.1,
+                 max_rounds: int = 6, words: int = 0, ctas_per_sm: int = 0):
+        self.rec, self.code = rec, rec.code
+        self.max_iter = int(max_iter)
+        self.f_start, self.df, self.max_rounds = float(f_start), float(df), int(max_rounds)
+        self.words, self.ctas = words, ctas_per_sm
+
+    def run(self, bob, syn, qber_host, known):
+        """bob, syn, known: device tensors for all frames; qber_host: numpy.
+        Returns dict of host arrays: bits, iters (summed over rounds), ok,
+        rounds, revealed, key_bits, f."""
+        dev = self.code.device
+        n, m = self.code.n, self.code.m
+        q = np.asarray(qber_host, dtype=np.float64)
+        B = q.size
+        p0, s0 = _rate.plan(n, m, q, self.f_start)
+        n_punct, n_short = p0.astype(np.int32).copy(), s0.astype(np.int32).copy()
+        revealed = np.zeros(B, np.int64)
+        rounds = np.zeros(B, np.int32)
+        iters_total = np.zeros(B, np.int64)
+        d_q = torch.from_numpy(q).to(dev)
+        out = (torch.zeros((B, self.code.nbytes), dtype=torch.uint8, device=dev),
+               torch.zeros((B,), dtype=torch.int32, device=dev),
+               torch.zeros((B,), dtype=torch.uint8, device=dev))
+        todo = np.arange(B, dtype=np.int32)
+        key0 = _rate.key_bits(n, p0, s0)
+        for rnd in range(self.max_rounds + 1):
+            d_np = torch.from_numpy(n_punct).to(dev)
+            d_ns = torch.from_numpy(n_short).to(dev)
+            d_list = torch.from_numpy(todo).to(dev)
+            self.code.reconcile_persistent(bob, d_q, syn, self.max_iter, rank=self.rec.rank, n_short=d_ns,
+                                           n_punct=d_np, known=known, frame_list=d_list,
+                                           llr_scale=self.rec.llr_scale, words=self.words,
+                                           ctas_per_sm=self.ctas, out=out)
+            ok = out[2].cpu().numpy()[todo].astype(bool)
+            it = out[1].cpu().numpy()[todo]
+            iters_total[todo] += it
+            rounds[todo] = rnd
+            todo = todo[~ok]
+            if todo.size == 0 or rnd == self.max_rounds:
+                break
+            # reveal more bits for the frames still failing
+            kb = key0[todo] - np.maximum(revealed[todo] - p0[todo], 0)
+            r = np.ceil(self.df * kb * _rate.h2(q[todo])).astype(np.int64)
+            revealed[todo] += r
+            n_short[todo] = (s0[todo] + revealed[todo]).astype(np.int32)
+            n_punct[todo] = np.maximum(p0[todo] - revealed[todo], 0).astype(np.int32)
+        rp = np.minimum(revealed, p0)
+        rk = revealed - rp
+        key = key0 - rk
+        leak = m - p0 + rp
+        f = leak / (key * _rate.h2(q))
+        bits, _, okd = (t.cpu().numpy() for t in out)
+        return dict(bits=bits, iters=iters_total, ok=okd, rounds=rounds, revealed=revealed, key_bits=key, f=f)

@@ -1,0 +1,78 @@
+"""The mixed-rate batch (autotuned persistent launch replayed from a CUDA
+graph) and the interactive rate-adaptation protocol, checked against the
+oracle frame by frame."""
+import numpy as np
+import pytest
+
+from oracle import core as orc
+from oracle import rate as orate
+from paper_1903_10107_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SCALE = 1 / 0.29
+
+
+def _code_and_frames(B, Z=32, seed=5):
+    degs = inputs.mixed_column_degrees(96, 0.3, 3, 6, seed)
+    base = inputs.qc_base_matrix(24, 96, Z, degs, seed)
+    n = 96 * Z
+    q = inputs.frame_qbers(B, 0.01, 0.08, seed)
+    xa = inputs.alice_keys(B, n, seed)
+    yb = xa ^ inputs.bsc_noise(B, n, q, seed)
+    tb = inputs.tiebreak_permutation(n, seed)
+    return base, Z, n, 24 * Z, q, xa, yb, tb
+
+
+def test_mixed_rate_batch_graph_matches_oracle():
+    from paper_1903_10107_gb300.pipeline import MixedRateBatch, Reconciler
+    base, Z, n, m, q, xa, yb, tb = _code_and_frames(45)
+    rec = Reconciler(base, Z, tb, llr_scale=SCALE)
+    p, s = rec.plan(q, 1.5)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    syn = rec.code.syndrome(c(xa))
+    mrb = MixedRateBatch(rec, 50).bind(c(yb), syn, c(q), c(p), c(s), c(xa))
+    assert mrb.graph is not None
+    for t in mrb.out:
+        t.zero_()
+    bits, iters, ok = (t.cpu().numpy() for t in mrb.run())
+    rank = orate.position_rank(base, Z, tb)
+    st = np.stack([orate.position_states(rank, int(p[f]), int(s[f])) for f in range(45)])
+    xa_u = inputs.unpack_bits(xa, n)
+    llr = orc.llr_frames(inputs.unpack_bits(yb, n), q, st, xa_u, scale=SCALE)
+    ob, oi, oo, _ = orc.decode(base, Z, llr, orc.syndrome(base, Z, xa_u), 50)
+    assert np.array_equal(ok, oo) and np.array_equal(iters, oi)
+    assert np.array_equal(inputs.unpack_bits(bits, n), ob)
+
+
+def test_interactive_protocol_matches_oracle_per_round_state():
+    from paper_1903_10107_gb300.pipeline import InteractiveProtocol, Reconciler
+    B = 48
+    base, Z, n, m, q, xa, yb, tb = _code_and_frames(B, seed=9)
+    rec = Reconciler(base, Z, tb, llr_scale=SCALE)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    syn = rec.code.syndrome(c(xa))
+    proto = InteractiveProtocol(rec, 40, f_start=1.1, df=0.15, max_rounds=5)
+    res = proto.run(c(yb), syn, q, c(xa))
+    assert res["rounds"].max() >= 1 and res["revealed"].max() > 0
+    # every frame's final result equals the oracle decode at its final reveal state
+    rank = orate.position_rank(base, Z, tb)
+    xa_u = inputs.unpack_bits(xa, n)
+    syn_u = orc.syndrome(base, Z, xa_u)
+    st = []
+    for f in range(B):
+        p0, s0 = orate.rate_plan(n, m, float(q[f]), 1.1)
+        r = int(res["revealed"][f])
+        st.append(orate.position_states(rank, max(p0 - r, 0), s0 + r))
+        # efficiency bookkeeping against the closed form: leak / (key * h(q))
+        rp = min(r, p0)
+        key = n - p0 - s0 - (r - rp)
+        f_ref = (m - p0 + rp) / (key * orate.binary_entropy(float(q[f])))
+        assert abs(res["f"][f] - f_ref) < 1e-9 and res["key_bits"][f] == key
+    llr = orc.llr_frames(inputs.unpack_bits(yb, n), q, np.stack(st), xa_u, scale=SCALE)
+    ob, oi, oo, _ = orc.decode(base, Z, llr, syn_u, 40)
+    assert np.array_equal(res["ok"], oo)
+    assert np.array_equal(inputs.unpack_bits(res["bits"], n), ob)
+    # frames that needed more rounds ended at a higher efficiency
+    assert (res["f"][res["rounds"] > 0] > 1.1).all()
