@@ -33,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1903_10107_gb300 import inputs, rate  # noqa: E402
+from paper_1903_10107_gb300 import inputs, rate, sharding  # noqa: E402
 
 DEFAULT_WORKLOAD = "n49152_mixed_q01_08"
 METRIC = "corrected-key Mbps on 1 GB300 at FER<=1e-2 and f~1.1 (QBER 1-8%); % HBM roofline"
@@ -273,8 +273,8 @@ def run_ours(args, rank, world, dist):
     w = inputs.WORKLOADS[args.workload]
     if args.max_iter:
         w.max_iter = args.max_iter
-    B = args.batch or w.batch
-    bt = Batch(w, B, rank * B)  # weak scaling: every rank its own B frames
+    first, B = sharding.weak_shard(args.batch or w.batch, rank, world)  # every rank its own frames
+    bt = Batch(w, B, first)
     rec = Reconciler(bt.base, w.Z, bt.tiebreak, dev, llr_scale=w.llr_scale)
     code = rec.code
     # Alice's syndromes (her side of the protocol; computed once, outside the step)
@@ -378,18 +378,10 @@ def run_ours(args, rank, world, dist):
         e2e_s, e_key, h2d, d2h = measure_e2e(args, rec, bt, d_syn, xa_bits, dev,
                                              shape.get("words_per_cta", 0), shape.get("ctas_per_sm", 0))
 
-    # max over ranks, sums over ranks
-    vals = np.array([step_s, e2e_s, corr_key, all_key, e_key, dec_s], dtype=np.float64)
-    if dist is not None:
-        t = torch.from_numpy(vals).to(dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        vals_max, vals_sum = tmax.cpu().numpy(), t.cpu().numpy()
-    else:
-        vals_max = vals_sum = vals
+    # max over ranks (times), sums over ranks (key bits)
+    vals_max, vals_sum = sharding.reduce_max_sum([step_s, e2e_s, dec_s], [corr_key, all_key, e_key], dist, dev)
     step_max, e2e_max = vals_max[0], vals_max[1]
-    corr_tot, all_tot, e_tot = vals_sum[2], vals_sum[3], vals_sum[4]
+    corr_tot, all_tot, e_tot = vals_sum[0], vals_sum[1], vals_sum[2]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
