@@ -173,6 +173,42 @@ int ldpc_reconcile_persistent(const ldpc_code* code, const uint8_t* bob_bits, co
  * and can be captured in a CUDA graph.  Synchronous. */
 int ldpc_code_reserve_persistent(ldpc_code* code, int list_len, int words, int ctas_per_sm);
 
+/* ldpc_decode_batch for callers that must not let the library allocate
+ * device memory.  The paper has no counterpart: this is a property of the
+ * library, not of the method.
+ *
+ * Who needs it: a reconciliation service that sizes all of its GPU memory at
+ * start-up and may not grow it while keys stream in; a process whose device
+ * memory is owned by another allocator's fixed pool; a latency-critical loop
+ * that cannot accept the device-wide synchronisation that cudaMalloc/cudaFree
+ * may cause.  ldpc_decode_batch keeps its message scratch in the code handle's
+ * arena and grows it with cudaMalloc; this entry point instead takes the
+ * scratch from one fixed 32 MiB array compiled into the library, and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Same arguments, layouts and results as ldpc_decode_batch (bit-identical
+ * outputs), with these differences:
+ *   - Limit: round_up(batch, frames per CTA) * edges bytes of scratch must fit
+ *     in 32 MiB (frames per CTA is 4, 8 or 16, chosen as in
+ *     ldpc_decode_batch); e.g. up to 2720 frames of the n=4096 code of 12288
+ *     edges, or up to 272 frames of a 122880-edge code.  Larger batches are
+ *     rejected with LDPC_EINVAL and a message giving the bytes needed; split
+ *     them into several calls.
+ *   - The array exists on every GPU that loads the library and stays there
+ *     until the process exits.
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current and caches it; make
+ *     the first call before any stream capture.  The code's device must be
+ *     the current device (else LDPC_EINVAL).
+ *   - All calls share the one array, which keeps the previous call's
+ *     contents.  Nothing needs clearing (the decoder never reads a message it
+ *     has not written in the same call), but two calls whose kernels overlap
+ *     on the GPU -- on different streams, or from different threads -- race
+ *     on the array and corrupt each other's results.  Serialise them. */
+int ldpc_decode_batch_noalloc(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome,
+                              int batch, int max_iter, uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok,
+                              void* stream);
+
 /* Device evaluation of the check-node table of Algorithm 1 exactly as the
  * decoder's byte-lane arithmetic computes it, for every (p, q) in
  * [0,128)^2: out[p*128 + q].  out: device, uint8[16384].  For tests. */

@@ -18,6 +18,8 @@
 //   * After each iteration all parity checks are tested with the latest E
 //     (section 2); lanes whose syndrome matches are frozen and leave the
 //     group's stopping test; the CTA stops when every lane has stopped.
+#include <mutex>
+
 #include "row_update.cuh"
 
 namespace {
@@ -242,6 +244,44 @@ int decode_common(const ldpc_code* c, const int8_t* llr, const uint8_t* syn, int
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Decoding without any device allocation.
+//
+// Some callers cannot let the library call cudaMalloc: a reconciliation
+// daemon that sized all of its device memory at start-up and must not grow it
+// while keys stream in, a process whose GPU memory belongs to another
+// allocator's fixed pool, or a latency-critical loop that cannot take the
+// device-wide synchronisation an allocation or free may cause.  For them the
+// decoder's message scratch comes from a fixed array compiled into this
+// library instead of the handle's arena.  The array occupies kStaticMsgBytes
+// on every GPU that loads the library, until the process exits.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticMsgBytes = (size_t)32 << 20;  // 32 MiB of message scratch
+__device__ __align__(256) uint32_t g_static_msg[kStaticMsgBytes / sizeof(uint32_t)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+uint32_t* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_msg on `device`, looked up once per device with
+// that device current (host code only knows the array's host-side stand-in).
+int static_msg_address(int device, uint32_t** out) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (device < 0 || device >= kMaxDevices) return ldpc::fail(LDPC_EUNSUPPORTED, "noalloc decode: device id");
+    if (!g_static_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_msg);
+        if (e != cudaSuccess) return ldpc::cuda_fail(e, "noalloc decode: cudaGetSymbolAddress");
+        g_static_addr[device] = static_cast<uint32_t*>(p);
+    }
+    *out = g_static_addr[device];
+    return LDPC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int ldpc_decode_batch(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome, int batch,
@@ -270,6 +310,45 @@ int ldpc_code_reserve(ldpc_code* code, int batch) {
     if (!code || batch < 0) return ldpc::fail(LDPC_EINVAL, "ldpc_code_reserve: bad argument");
     const size_t need = (size_t)((batch + 15) / 16) * 16 * (size_t)code->edges;
     return ldpc::ensure_arena(code, need);
+}
+
+// Same decode as ldpc_decode_batch, with the message scratch taken from the
+// library's fixed device array instead of the handle's arena; see the header.
+int ldpc_decode_batch_noalloc(const ldpc_code* code, const int8_t* llr_in, const uint8_t* target_syndrome,
+                              int batch, int max_iter, uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok,
+                              void* stream) {
+    using ldpc::fail;
+    const ldpc_code* c = code;
+    if (!c) return fail(LDPC_EINVAL, "noalloc decode: NULL code");
+    if (batch < 0) return fail(LDPC_EINVAL, "noalloc decode: negative batch");
+    if (max_iter < 1) return fail(LDPC_EINVAL, "noalloc decode: max_iter must be >= 1");
+    if (batch == 0) return LDPC_OK;
+    if (!llr_in || !target_syndrome || !out_bits || !out_iters || !out_ok)
+        return fail(LDPC_EINVAL, "noalloc decode: NULL buffer");
+    int cur = -1;
+    LDPC_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != c->device) return fail(LDPC_EINVAL, "noalloc decode: make the code's device current first");
+    const int smem_limit = ldpc::max_dyn_smem(c->device);
+    if ((int64_t)smem_bytes(c, 1) > smem_limit)
+        return fail(LDPC_EUNSUPPORTED, "noalloc decode: soft values of four frames exceed shared memory");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int W = pick_words(c, batch, smem_limit, sms);
+    const int64_t groups = (batch + 4 * W - 1) / (4 * W);
+    const size_t need = (size_t)groups * 4 * W * (size_t)c->edges;
+    if (need > kStaticMsgBytes)
+        return fail(LDPC_EINVAL, "noalloc decode: " + std::to_string(batch) + " frames need " + std::to_string(need) +
+                                     " bytes of message scratch; the fixed scratch holds " +
+                                     std::to_string(kStaticMsgBytes) + " bytes (decode fewer frames per call)");
+    uint32_t* msg = nullptr;
+    int rc = static_msg_address(c->device, &msg);
+    if (rc) return rc;
+    DecodeArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, llr_in, target_syndrome, batch, max_iter, nullptr,
+                 nullptr, out_bits, out_iters, out_ok, msg};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (W == 1) return launch_w<1, false>(c, A, (int)groups, st);
+    if (W == 2) return launch_w<2, false>(c, A, (int)groups, st);
+    return launch_w<4, false>(c, A, (int)groups, st);
 }
 
 }  // extern "C"

@@ -42,6 +42,7 @@ SIGNATURES = {
     "ldpc_decode_batch_words": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P]),
     "ldpc_reconcile_persistent": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _D, _I, _I, _P, _P, _P, _P]),
     "ldpc_code_reserve_persistent": (_I, [_P, _I, _I, _I]),
+    "ldpc_decode_batch_noalloc": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "ldpc_debug_tau_table": (_I, [_P, _P]),
     "ldpc_launch_count": (_I64, []),
     "ldpc_strerror": (ctypes.c_char_p, [_I]),
@@ -143,6 +144,11 @@ def ldpc_reconcile_persistent(code, bob_bits, qber, rank, n_short, n_punct, know
 
 def ldpc_code_reserve_persistent(code, list_len, words, ctas_per_sm):
     _call("ldpc_code_reserve_persistent", code, list_len, words, ctas_per_sm)
+
+
+def ldpc_decode_batch_noalloc(code, llr_in, target_syndrome, batch, max_iter, out_bits, out_iters, out_ok, stream):
+    _call("ldpc_decode_batch_noalloc", code, llr_in, target_syndrome, batch, max_iter, out_bits, out_iters, out_ok,
+          stream)
 
 
 def ldpc_debug_tau_table(out, stream):
