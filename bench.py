@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--max-iter", type=int, default=0, help="override the workload's iteration cap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-order", action="store_true", help="persistent launch takes frames in index order")
     ap.add_argument("--protocol", choices=["fixed", "interactive"], default="fixed",
                     help="fixed: one rate per frame for the workload's target f; interactive: rounds of reveal")
     ap.add_argument("--f-start", type=float, default=1.1)
@@ -265,7 +266,7 @@ def measure_e2e(args, rec, bt, d_syn, xa_bits, dev, words=0, ctas=0):
 def run_ours(args, rank, world, dist):
     import torch
     from paper_1903_10107_gb300 import native
-    from paper_1903_10107_gb300.pipeline import MixedRateBatch, Reconciler
+    from paper_1903_10107_gb300.pipeline import MixedRateBatch, Reconciler, hardest_first
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -293,7 +294,8 @@ def run_ours(args, rank, world, dist):
 
     if mixed:
         # one persistent launch (LLR quantisation fused), replayed from a CUDA graph
-        mrb = MixedRateBatch(rec, w.max_iter).bind(d_yb, d_syn, d_q, d_np, d_ns, d_kn)
+        order = None if args.no_order else hardest_first(bt.n_punct, bt.n_short, bt.q)
+        mrb = MixedRateBatch(rec, w.max_iter).bind(d_yb, d_syn, d_q, d_np, d_ns, d_kn, order=order)
         l0 = native.ldpc_launch_count()
         mrb._launch(mrb.words, mrb.ctas)
         torch.cuda.synchronize()
@@ -301,7 +303,8 @@ def run_ours(args, rank, world, dist):
         out = mrb.out
         step = mrb.run
         kernel_name = "persistent_kernel"
-        shape = {"words_per_cta": mrb.words, "ctas_per_sm": mrb.ctas, "cuda_graph": mrb.graph is not None}
+        shape = {"words_per_cta": mrb.words, "ctas_per_sm": mrb.ctas, "cuda_graph": mrb.graph is not None,
+                 "work_order": "given" if order is None else "hardest first"}
     else:
         code.reserve(B)
         out = (torch.empty((B, code.nbytes), dtype=torch.uint8, device=dev),

@@ -77,6 +77,13 @@ class Reconciler:
         return tuple(outs), h2d, d2h
 
 
+def hardest_first(n_punct, n_short, qber) -> np.ndarray:
+    """Frame order for the persistent launch: descending punctured count
+    (puncturing is what makes a frame slow or fail at a given efficiency),
+    then descending QBER."""
+    return np.lexsort((-np.asarray(qber), -np.asarray(n_punct))).astype(np.int32)
+
+
 def corrected_frames(bits: np.ndarray, ok: np.ndarray, alice: np.ndarray) -> np.ndarray:
     """Frames whose decoder reported success and whose decoded word equals
     Alice's key (undetected errors do not count as corrected)."""
@@ -105,19 +112,25 @@ class MixedRateBatch:
 
     def _launch(self, words, ctas, n_frames=None):
         b = self.buffers
-        B = b["bob"].shape[0] if n_frames is None else n_frames
         sl = (lambda t: t) if n_frames is None else (lambda t: None if t is None else t[:n_frames])
         out = self.out if n_frames is None else tuple(t[:n_frames] for t in self.out)
+        order = self.order if n_frames is None else None
         return self.code.reconcile_persistent(sl(b["bob"]), sl(b["qber"]), sl(b["syn"]), self.max_iter,
                                               rank=self.rec.rank if b["n_punct"] is not None else None,
                                               n_short=sl(b["n_short"]), n_punct=sl(b["n_punct"]),
-                                              known=sl(b["known"]), llr_scale=self.rec.llr_scale,
-                                              words=words, ctas_per_sm=ctas, out=out)
+                                              known=sl(b["known"]), frame_list=order,
+                                              llr_scale=self.rec.llr_scale, words=words, ctas_per_sm=ctas, out=out)
 
-    def bind(self, bob, syn, qber, n_punct=None, n_short=None, known=None):
+    def bind(self, bob, syn, qber, n_punct=None, n_short=None, known=None, order=None):
+        """``order``: optional host array, the order in which lanes take the
+        frames.  Frames likely to need many iterations (most punctured) should
+        come first, so that their long decodes overlap the rest instead of
+        running alone at the end of the launch."""
         from . import autotune
         B = bob.shape[0]
         self.buffers = dict(bob=bob, syn=syn, qber=qber, n_punct=n_punct, n_short=n_short, known=known)
+        self.order = None if order is None else torch.from_numpy(
+            np.ascontiguousarray(order, dtype=np.int32)).to(self.code.device)
         dev = self.code.device
         self.out = (torch.zeros((B, self.code.nbytes), dtype=torch.uint8, device=dev),
                     torch.zeros((B,), dtype=torch.int32, device=dev),
