@@ -173,6 +173,46 @@ int ldpc_reconcile_persistent(const ldpc_code* code, const uint8_t* bob_bits, co
  * and can be captured in a CUDA graph.  Synchronous. */
 int ldpc_code_reserve_persistent(ldpc_code* code, int list_len, int words, int ctas_per_sm);
 
+/* FP32 relaxation of the layered decoder, for learning check-node
+ * corrections (the normalised/offset forms section 2 lists as alternatives).
+ * Same schedule, sign rule (Eq. 1 with the syndrome sign) and forward-backward
+ * fold of Eq. 7 as ldpc_decode_batch, in float and without saturation; the
+ * fold uses the tempered box-plus beta_k(x,y) = k*beta(x/k, y/k) of Eq. 6,
+ * which is what Algorithm 1's table (the integer form of beta at its own step
+ * D_t, section 3.2) computes when LLRs are quantised at a step D (k = D/D_t;
+ * k = 1 is exact belief propagation).  Each magnitude becomes
+ *   alpha[t][c] * relu(fold - gamma[t][c])
+ * for iteration t and the layer's row-degree class c.  A degree-1 row sends
+ * 50 (the empty box-plus).  Variable update: plain Eq. 9.
+ *   llr   : device, float[batch][n] channel LLRs in nats (positive = bit 0).
+ *   syn   : device, uint8[batch][ceil(m/8)] target syndromes.
+ *   bits  : device, uint8[batch][ceil(n/8)] Alice's bits, or NULL (no loss).
+ *   alpha, gamma : device, float[iters][n_classes].
+ *   layer_class  : device, int32[Mb] class of each layer (0..n_classes-1).
+ *   ckE   : device, float[iters+1][batch][n]: E at the start of every
+ *           iteration and the final E (checkpoints for the adjoint).
+ *   ckL   : device, float[iters][batch][edges]: messages at the start of
+ *           iterations 1..iters-1 (slot 0 is not written: L starts at 0).
+ *   loss  : device float[1] (zeroed here), or NULL: mean over frames and bits
+ *           of softplus(-(1-2x) E_final), the cross entropy against Alice.
+ * Requires Z <= 512 and row degree <= 32. */
+int ldpc_relaxed_forward(const ldpc_code* code, const float* llr, const uint8_t* syn, const uint8_t* bits, int batch,
+                         int iters, const float* alpha, const float* gamma, const int32_t* layer_class,
+                         int n_classes, float kappa, float* ckE, float* ckL, float* loss, void* stream);
+
+/* Adjoint of ldpc_relaxed_forward's loss with respect to alpha and gamma
+ * (and optionally the LLRs).  Walks the iterations backwards; each iteration
+ * is recomputed from its checkpoint (ckE, ckL) and its layers reversed with
+ * d beta_k/dx = s((x+y)/k) - s((x-y)/k), s the logistic function.
+ *   V, gL : device scratch, float[batch][edges] each.
+ *   grad_alpha, grad_gamma : device, float[iters][n_classes] (zeroed here).
+ *   grad_llr : device, float[batch][n], or NULL.
+ * Gradients of sign and relu at 0 are taken as 0 (as autograd does). */
+int ldpc_relaxed_backward(const ldpc_code* code, const uint8_t* syn, const uint8_t* bits, int batch, int iters,
+                          const float* alpha, const float* gamma, const int32_t* layer_class, int n_classes,
+                          float kappa, const float* ckE, const float* ckL, float* V, float* gL, float* grad_alpha,
+                          float* grad_gamma, float* grad_llr, void* stream);
+
 /* ldpc_decode_batch for callers that must not let the library allocate
  * device memory.  The paper has no counterpart: this is a property of the
  * library, not of the method.

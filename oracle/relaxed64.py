@@ -2,17 +2,25 @@
 (test infrastructure only).
 
 The relaxation keeps the layered schedule of section 2 but computes in
-floating point: the check-node magnitude is the exact box-plus of Eq. 6,
-folded over the other edges of the row in the same forward-backward order
-as the integer decoder (Eq. 7), then scaled and offset per iteration t and
-row-degree class c (the normalised/offset forms listed in section 2):
+floating point.  Algorithm 1's table is the integer representation of the
+box-plus beta of Eq. 6 at its own quantisation step D_t (section 3.2); an
+integer decoder fed channel LLRs at a finer step D therefore computes, in
+nats, the tempered box-plus
 
-    mag_k = alpha[t, c] * relu(boxplus_{k' != k} |L_k'i| - gamma[t, c])
+    beta_k(x, y) = k * beta(x / k, y / k),   k = D / D_t,
+
+which is exact belief propagation for k = 1 and tends to min-sum as k -> 0.
+The relaxation folds beta_k over the other edges of the row in the same
+forward-backward order as the integer decoder (Eq. 7), then scales and
+offsets per iteration t and row-degree class c (the normalised/offset forms
+listed in section 2):
+
+    mag_k = alpha[t, c] * relu(fold_{k' != k} |L_k'i| - gamma[t, c])
 
 There is no saturation, so Algorithm 2's guard does not apply and the
 variable-node update is the plain Eq. 9.  The loss is the mean binary cross
 entropy of the final soft values against Alice's bits (soft value E > 0
-means bit 0).  alpha = 1, gamma = 0 gives exact layered belief propagation.
+means bit 0).  A degree-1 row sends the constant EMPTY (the empty box-plus).
 
 ``decode`` is numpy; ``loss_and_grad`` builds the same computation from
 torch fp64 CPU operations so that autograd supplies a reference gradient.
@@ -22,9 +30,13 @@ from __future__ import annotations
 import numpy as np
 
 
-def boxplus(x, y):
-    """beta(x, y) of Eq. 6 for x, y >= 0, in a form that stays finite."""
-    return np.minimum(x, y) + np.log1p(np.exp(-(x + y))) - np.log1p(np.exp(-np.abs(x - y)))
+EMPTY = 50.0
+
+
+def boxplus(x, y, kappa=1.0):
+    """beta_k(x, y) = k * beta(x/k, y/k), beta of Eq. 6, for x, y >= 0, in a
+    form that stays finite."""
+    return np.minimum(x, y) + kappa * (np.log1p(np.exp(-(x + y) / kappa)) - np.log1p(np.exp(-np.abs(x - y) / kappa)))
 
 
 def layer_tables(base, Z):
@@ -69,7 +81,7 @@ def _exclusive_boxplus(a, bp, xp):
     return xp.stack(outs, axis=1)
 
 
-def decode(base, Z, llr, syn, iters, alpha=None, gamma=None, stop=False):
+def decode(base, Z, llr, syn, iters, alpha=None, gamma=None, stop=False, kappa=1.0):
     """Relaxed layered decoding.  llr: float [B][n] (positive = bit 0),
     syn: 0/1 [B][m].  alpha, gamma: [iters][classes] or None (1, 0).
     Returns the final soft values E [B][n] (and, with stop=True, the
@@ -90,11 +102,11 @@ def decode(base, Z, llr, syn, iters, alpha=None, gamma=None, stop=False):
             v = E[:, J] - Lold
             s = np.where(v < 0, -1.0, 1.0)
             S = ssign[:, i * Z:(i + 1) * Z][:, None, :] * np.prod(s, axis=1, keepdims=True)
-            mag = _exclusive_boxplus(np.abs(v), boxplus, np)
+            mag = _exclusive_boxplus(np.abs(v), lambda a, b: boxplus(a, b, kappa), np)
             al = 1.0 if alpha is None else alpha[t, cls[i]]
             ga = 0.0 if gamma is None else gamma[t, cls[i]]
             if d == 1:
-                mag = np.full_like(mag, 1e30)
+                mag = np.full_like(mag, EMPTY)
             mag = al * np.maximum(mag - ga, 0.0)
             Ln = S * s * mag
             E[:, J] = v + Ln
@@ -111,7 +123,7 @@ def decode(base, Z, llr, syn, iters, alpha=None, gamma=None, stop=False):
     return (E, done) if stop else E
 
 
-def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma):
+def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma, kappa=1.0):
     """Mean BCE of the final E against Alice's bits, and its gradient with
     respect to alpha and gamma, by torch fp64 autograd on the CPU."""
     import torch
@@ -127,7 +139,8 @@ def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma):
     ssign = torch.tensor(1.0 - 2.0 * np.asarray(syn, dtype=np.float64))
 
     def bp(x, y):
-        return torch.minimum(x, y) + torch.log1p(torch.exp(-(x + y))) - torch.log1p(torch.exp(-(x - y).abs()))
+        return torch.minimum(x, y) + kappa * (torch.log1p(torch.exp(-(x + y) / kappa))
+                                              - torch.log1p(torch.exp(-(x - y).abs() / kappa)))
 
     for t in range(T):
         for i, (J, off, d) in enumerate(tabs):
@@ -139,7 +152,7 @@ def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma):
             s = torch.where(v < 0, -1.0, 1.0).to(torch.float64)
             S = ssign[:, i * Z:(i + 1) * Z][:, None, :] * torch.prod(s, dim=1, keepdim=True)
             if d == 1:
-                mag = torch.full_like(v, 1e30)
+                mag = torch.full_like(v, EMPTY)
             else:
                 mag = _exclusive_boxplus(v.abs(), bp, torch)
             mag = al[t, cls[i]] * torch.relu(mag - ga[t, cls[i]])

@@ -42,6 +42,9 @@ SIGNATURES = {
     "ldpc_decode_batch_words": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P]),
     "ldpc_reconcile_persistent": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _D, _I, _I, _P, _P, _P, _P]),
     "ldpc_code_reserve_persistent": (_I, [_P, _I, _I, _I]),
+    "ldpc_relaxed_forward": (_I, [_P, _P, _P, _P, _I, _I, _P, _P, _P, _I, ctypes.c_float, _P, _P, _P, _P]),
+    "ldpc_relaxed_backward": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P,
+                                   _P]),
     "ldpc_decode_batch_noalloc": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "ldpc_debug_tau_table": (_I, [_P, _P]),
     "ldpc_launch_count": (_I64, []),
@@ -144,6 +147,18 @@ def ldpc_reconcile_persistent(code, bob_bits, qber, rank, n_short, n_punct, know
 
 def ldpc_code_reserve_persistent(code, list_len, words, ctas_per_sm):
     _call("ldpc_code_reserve_persistent", code, list_len, words, ctas_per_sm)
+
+
+def ldpc_relaxed_forward(code, llr, syn, bits, batch, iters, alpha, gamma, layer_class, n_classes, kappa, ckE, ckL,
+                         loss, stream):
+    _call("ldpc_relaxed_forward", code, llr, syn, bits, batch, iters, alpha, gamma, layer_class, n_classes, kappa, ckE,
+          ckL, loss, stream)
+
+
+def ldpc_relaxed_backward(code, syn, bits, batch, iters, alpha, gamma, layer_class, n_classes, kappa, ckE, ckL, V, gL,
+                          grad_alpha, grad_gamma, grad_llr, stream):
+    _call("ldpc_relaxed_backward", code, syn, bits, batch, iters, alpha, gamma, layer_class, n_classes, kappa, ckE,
+          ckL, V, gL, grad_alpha, grad_gamma, grad_llr, stream)
 
 
 def ldpc_decode_batch_noalloc(code, llr_in, target_syndrome, batch, max_iter, out_bits, out_iters, out_ok, stream):

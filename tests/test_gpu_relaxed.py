@@ -1,0 +1,100 @@
+"""The FP32 relaxed decoder and its hand-written adjoint against the FP64
+reference: forward within 1e-4 relative, gradient within 1e-3 relative, and
+the adjoint against finite differences of the GPU loss."""
+import numpy as np
+import pytest
+
+from oracle import relaxed64 as rx
+from paper_1903_10107_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _case(Mb=4, Nb=12, Z=16, B=6, seed=0, mu=2.0, sigma=1.5):
+    base = inputs.qc_base_matrix(Mb, Nb, Z, 3, seed)
+    g = np.random.default_rng(seed)
+    n = Nb * Z
+    xa = g.integers(0, 2, size=(B, n)).astype(np.uint8)
+    from oracle import core as orc
+    syn = orc.syndrome(base, Z, xa)
+    llr = ((1 - 2.0 * xa) * mu + g.normal(0, sigma, size=(B, n))).astype(np.float32)
+    return base, Z, llr, syn, xa
+
+
+def _gpu(base, Z, llr, syn, xa, al, ga, kappa, iters):
+    from paper_1903_10107_gb300.decoder import QCCode
+    from paper_1903_10107_gb300.relaxed import RelaxedDecodeFn, degree_classes
+    code = QCCode(base, Z)
+    cls = torch.from_numpy(degree_classes(base)[0]).cuda()
+    A = torch.tensor(al, dtype=torch.float32, device="cuda", requires_grad=True)
+    G = torch.tensor(ga, dtype=torch.float32, device="cuda", requires_grad=True)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    loss, E = RelaxedDecodeFn.apply(A, G, code, c(llr), c(inputs.pack_bits(syn)), c(inputs.pack_bits(xa)), cls,
+                                    kappa)
+    loss.backward()
+    return float(loss), E.cpu().numpy(), A.grad.cpu().numpy(), G.grad.cpu().numpy(), code, cls
+
+
+@pytest.mark.parametrize("kappa", [1.0, 0.431])
+def test_forward_matches_fp64_reference(kappa):
+    base, Z, llr, syn, xa = _case()
+    T = 6
+    C = len(rx.degree_classes(base)[1])
+    g = np.random.default_rng(1)
+    al, ga = g.uniform(0.7, 1.1, (T, C)), g.uniform(0.0, 0.3, (T, C))
+    loss, E, _, _, _, _ = _gpu(base, Z, llr, syn, xa, al, ga, kappa, T)
+    E64 = rx.decode(base, Z, llr.astype(np.float64), syn, T, al.astype(np.float32).astype(np.float64),
+                    ga.astype(np.float32).astype(np.float64), kappa=kappa)
+    rel = np.abs(E - E64) / np.maximum(np.abs(E64), 1.0)
+    assert rel.max() <= 1e-4, rel.max()
+
+
+@pytest.mark.parametrize("kappa", [1.0, 0.431])
+def test_gradient_matches_fp64_reference(kappa):
+    base, Z, llr, syn, xa = _case(seed=3)
+    T = 5
+    C = len(rx.degree_classes(base)[1])
+    g = np.random.default_rng(2)
+    al = g.uniform(0.7, 1.1, (T, C)).astype(np.float32).astype(np.float64)
+    ga = g.uniform(0.05, 0.3, (T, C)).astype(np.float32).astype(np.float64)
+    loss, E, g_al, g_ga, _, _ = _gpu(base, Z, llr, syn, xa, al, ga, kappa, T)
+    l64, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=kappa)
+    assert abs(loss - l64) <= 1e-4 * abs(l64)
+    ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
+    got = np.concatenate([g_al.ravel(), g_ga.ravel()])
+    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
+
+
+def test_gradient_matches_finite_differences_of_gpu_loss():
+    from paper_1903_10107_gb300.relaxed import RelaxedDecodeFn
+    base, Z, llr, syn, xa = _case(seed=5, B=16)
+    T = 4
+    C = len(rx.degree_classes(base)[1])
+    g = np.random.default_rng(6)
+    al, ga = g.uniform(0.8, 1.1, (T, C)), g.uniform(0.05, 0.25, (T, C))
+    loss, E, g_al, g_ga, code, cls = _gpu(base, Z, llr, syn, xa, al, ga, 0.7, T)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (code, c(llr), c(inputs.pack_bits(syn)), c(inputs.pack_bits(xa)), cls, 0.7)
+    # directional derivative along a random direction, central differences in fp32
+    dA, dG = g.normal(size=al.shape), g.normal(size=ga.shape)
+    eps = 2e-3
+
+    def L(sgn):
+        A = torch.tensor(al + sgn * eps * dA, dtype=torch.float32, device="cuda")
+        G = torch.tensor(ga + sgn * eps * dG, dtype=torch.float32, device="cuda")
+        with torch.no_grad():
+            return float(RelaxedDecodeFn.apply(A, G, *args)[0])
+    fd = (L(1) - L(-1)) / (2 * eps)
+    an = float((g_al * dA).sum() + (g_ga * dG).sum())
+    assert abs(fd - an) <= 2e-2 * abs(an) + 1e-6, (fd, an)
+
+
+def test_identity_tables_round_to_plain_decoder():
+    from paper_1903_10107_gb300.decoder import QCCode
+    from paper_1903_10107_gb300.relaxed import RelaxedDecoder
+    w = inputs.WORKLOADS["n4096_r075_q02"]
+    code = QCCode(w.base(), w.Z)
+    m = RelaxedDecoder(code, 20)
+    sq, oq = m.integer_tables(8.0)
+    assert sq.shape == (20, w.Mb) and (sq == 16).all() and (oq == 0).all()

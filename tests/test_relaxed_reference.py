@@ -1,0 +1,90 @@
+"""Pins of the FP64 relaxed-decoder reference (oracle/relaxed64.py) against
+closed forms and finite differences."""
+import numpy as np
+import pytest
+
+from oracle import relaxed64 as rx
+
+
+def _gauss_case(Mb=3, Nb=9, Z=4, B=3, seed=0):
+    from paper_1903_10107_gb300 import inputs
+    base = inputs.qc_base_matrix(Mb, Nb, Z, 2, seed)
+    g = np.random.default_rng(seed)
+    n, m = Nb * Z, Mb * Z
+    xa = g.integers(0, 2, size=(B, n))
+    H = np.zeros((m, n), np.int64)
+    for i in range(Mb):
+        for k in range(Nb):
+            if base[i, k] >= 0:
+                for r in range(Z):
+                    H[i * Z + r, k * Z + (r + base[i, k]) % Z] = 1
+    syn = (xa @ H.T) % 2
+    llr = (1 - 2 * xa) * 2.0 + g.normal(0, 1.5, size=(B, n))  # continuous: no sign/relu kinks
+    return base, Z, llr, syn, xa
+
+
+def test_single_check_equals_tanh_rule():
+    """One check of degree d (Z = 1): after one iteration E_k = llr_k +
+    (-1)^s prod_{k'!=k} sign * 2 atanh(prod tanh(|llr_k'|/2))  (Eqs. 1, 2, 9)."""
+    g = np.random.default_rng(3)
+    for d in (2, 3, 5, 7):
+        base = np.zeros((1, d), np.int32)
+        llr = g.normal(0, 3, size=(2, d))
+        syn = np.array([[0], [1]])
+        E = rx.decode(base, 1, llr, syn, 1)
+        for f in range(2):
+            for k in range(d):
+                o = np.delete(llr[f], k)
+                mag = 2 * np.arctanh(np.prod(np.tanh(np.abs(o) / 2)))
+                sign = (-1) ** syn[f, 0] * np.prod(np.sign(o))
+                assert abs(E[f, k] - (llr[f, k] + sign * mag)) < 1e-10
+
+
+def test_tempered_boxplus_limits():
+    g = np.random.default_rng(4)
+    x, y = g.uniform(0, 10, 500), g.uniform(0, 10, 500)
+    for kappa in (1.0, 0.5, 0.1, 0.01):
+        b = rx.boxplus(x, y, kappa)
+        assert np.all(b <= np.minimum(x, y) + 1e-12)
+        assert np.all(b >= np.minimum(x, y) - kappa * np.log(2) - 1e-12)  # -> min-sum as kappa -> 0
+    # kappa = 1 is Eq. 6's tanh form
+    t = 2 * np.arctanh(np.tanh(x / 2) * np.tanh(y / 2))
+    ok = t < 15
+    assert np.allclose(rx.boxplus(x, y)[ok], t[ok], rtol=1e-9, atol=1e-12)
+
+
+def test_numpy_and_torch_forms_agree():
+    pytest.importorskip("torch")
+    base, Z, llr, syn, xa = _gauss_case()
+    T = 3
+    C = len(rx.degree_classes(base)[1])
+    g = np.random.default_rng(5)
+    al, ga = g.uniform(0.7, 1.2, (T, C)), g.uniform(0.0, 0.3, (T, C))
+    E_np = rx.decode(base, Z, llr, syn, T, al, ga, kappa=0.6)
+    _, _, _, E_t = rx.loss_and_grad(base, Z, llr, syn, xa, al, ga, kappa=0.6)
+    assert np.allclose(E_np, E_t, rtol=1e-12, atol=1e-12)
+
+
+def test_reference_gradient_matches_finite_differences():
+    pytest.importorskip("torch")
+    base, Z, llr, syn, xa = _gauss_case(seed=7)
+    T = 3
+    C = len(rx.degree_classes(base)[1])
+    g = np.random.default_rng(8)
+    al, ga = g.uniform(0.7, 1.2, (T, C)), g.uniform(0.05, 0.3, (T, C))
+    loss, g_al, g_ga, _ = rx.loss_and_grad(base, Z, llr, syn, xa, al, ga, kappa=0.7)
+    eps = 1e-6
+    for (t, c) in [(0, 0), (1, C - 1), (T - 1, 0)]:
+        for which, grad in (("a", g_al), ("g", g_ga)):
+            p, m = al.copy(), al.copy()
+            q, r = ga.copy(), ga.copy()
+            if which == "a":
+                p[t, c] += eps; m[t, c] -= eps
+                lp = rx.loss_and_grad(base, Z, llr, syn, xa, p, ga, kappa=0.7)[0]
+                lm = rx.loss_and_grad(base, Z, llr, syn, xa, m, ga, kappa=0.7)[0]
+            else:
+                q[t, c] += eps; r[t, c] -= eps
+                lp = rx.loss_and_grad(base, Z, llr, syn, xa, al, q, kappa=0.7)[0]
+                lm = rx.loss_and_grad(base, Z, llr, syn, xa, al, r, kappa=0.7)[0]
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - grad[t, c]) <= 1e-6 + 1e-5 * abs(fd), (which, t, c, fd, grad[t, c])
