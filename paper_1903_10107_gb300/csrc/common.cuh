@@ -92,23 +92,50 @@ __device__ __forceinline__ uint32_t lt_u8(uint32_t x, uint32_t y) {
     return ((~x & y) | (~(x ^ y) & ~c)) & kHigh;
 }
 
+// Integer multiply-add on the FMA pipe.  The decoder's byte-lane arithmetic
+// is otherwise all integer-ALU work (adds, logic, shifts), and the ALU pipe
+// issues at half the rate of the scheduler; an add written as x * 1 + c, or a
+// right shift by 7 written as the high word of x * 2^25, runs on the
+// multiply-add pipe instead and the two pipes then share the load.  The
+// multipliers come from constant memory so that the compiler cannot fold
+// them back into plain adds and shifts.
+__device__ __forceinline__ uint32_t imad(uint32_t x, uint32_t y, uint32_t z) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(y), "r"(z));
+    return d;
+}
+__device__ __forceinline__ uint32_t imad_hi(uint32_t x, uint32_t y, uint32_t z) {
+    uint32_t d;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(y), "r"(z));
+    return d;
+}
+static __constant__ uint32_t c_mul[2] = {1u, 1u << 25};  // {x -> x, hi(x * 2^25) = x >> 7}
+
 // tau(a, b) of Algorithm 1 per byte, for a, b in [0, 127] (= MSG_max, so the
 // input caps are the identity).
 //   l = min, d = |a - b|;  l > 2: l - [d<2] - [d<6];  else max(l - [d<4], 0)
-// l = (a + b - d) / 2 (a + b <= 254 fits a byte).  The tests "x >= c" are
-// bit 7 of x + (128 - c), which stays below 256 for x <= 127.  For l <= 2
-// the correction [d<4] is applied only where l >= 1, which equals max(., 0).
+// a + b - d = 2 l per byte (a + b <= 254 fits a byte); every byte of it is
+// even, so the 32-bit shift by one brings a zero into each byte's bit 7 and
+// yields l exactly.  The tests "x >= c" are bit 7 of x + (128 - c), which
+// stays below 256 for x <= 127.  For l <= 2 the correction [d<4] is applied
+// only where l >= 1, which equals max(., 0).  The result l - c1 - c2 (c1, c2
+// the 0/1 corrections) is formed as l - 2 + (1 - c1) + (1 - c2): n1, n2 hold
+// 1 - c1, 1 - c2 in bit 7, and the sum is exact as 32-bit arithmetic because
+// the final bytes l - c1 - c2 lie in [0, 127].
 __device__ __forceinline__ uint32_t tau(uint32_t a, uint32_t b) {
+    const uint32_t one = c_mul[0];
     const uint32_t d = absdiff(a, b);
-    const uint32_t l = ((a + b - d) >> 1) & kMax;
-    const uint32_t d_ge2 = d + 0x7E7E7E7Eu;
-    const uint32_t d_ge4 = d + 0x7C7C7C7Cu;
-    const uint32_t d_ge6 = d + 0x7A7A7A7Au;
-    const uint32_t l_ge3 = l + 0x7D7D7D7Du;
-    const uint32_t l_ge1 = l + 0x7F7F7F7Fu;
-    const uint32_t c2 = l_ge3 & ~d_ge2 & kHigh;                                 // l>=3 and d<2
-    const uint32_t c1 = ((l_ge3 & ~d_ge6) | (~l_ge3 & ~d_ge4)) & l_ge1 & kHigh; // l>=3 ? d<6 : (l>=1 and d<4)
-    return l - (c2 >> 7) - (c1 >> 7);                                          // corrections <= l, no borrow
+    const uint32_t l = (a + b - d) >> 1;
+    const uint32_t d_ge2 = imad(d, one, 0x7E7E7E7Eu);
+    const uint32_t d_ge4 = imad(d, one, 0x7C7C7C7Cu);
+    const uint32_t d_ge6 = imad(d, one, 0x7A7A7A7Au);
+    const uint32_t l_ge3 = imad(l, one, 0x7D7D7D7Du);
+    const uint32_t l_ge1 = imad(l, one, 0x7F7F7F7Fu);
+    const uint32_t n2 = ~(l_ge3 & ~d_ge2) & kHigh;                                  // not (l>=3 and d<2)
+    const uint32_t n1 = ~(((l_ge3 & ~d_ge6) | (~l_ge3 & ~d_ge4)) & l_ge1) & kHigh;  // not (l>=3 ? d<6 : l>=1 and d<4)
+    uint32_t t = imad(l, one, 0xFDFDFDFEu);                                         // l - 0x02020202 (mod 2^32)
+    t = imad_hi(n1, c_mul[1], t);
+    return imad_hi(n2, c_mul[1], t);
 }
 
 // Four syndrome bits (bit l = frame l) -> bit 7 of byte l.  For a 4-bit

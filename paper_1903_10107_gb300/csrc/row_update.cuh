@@ -97,14 +97,20 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
     int idx[HMAX];
     uint32_t S = (half == 0 && valid) ? nibble_to_high(syn_nib) : 0u;
 
+    const bool load_l = C.fresh != 0xFFFFFFFFu;
 #pragma unroll(HMAX)
     for (int j = 0; j < HMAX; ++j) {
         if (j < cnt) {
+            av[j] = load_l ? Lp[j * Lstep] : kHigh;  // every message load of the row in flight first
             const int2 t = et[j * kdir];
             idx[j] = t.x + wrap(r + t.y, Z) * W + C.w;
+        }
+    }
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < cnt) {
             const uint32_t e = C.E_s[idx[j]];
-            uint32_t lb = kHigh;                 // offset-binary zero
-            if (C.fresh != 0xFFFFFFFFu) lb = select(C.fresh, kHigh, Lp[j * Lstep]);
+            const uint32_t lb = select(C.fresh, kHigh, av[j]);  // stale lanes read as 0
             const uint32_t sv = lt_u8(e, lb);    // sign of E - L
             av[j] = cap127(absdiff(e, lb)) | sv; // |sat8(E - L)| and its sign
             S ^= sv;
@@ -136,15 +142,20 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
             if (j > 0) R = rvalid ? tau(a, R) : a;
             rvalid = true;
             if (TABLES) m = apply_table(m, C.sq, C.oq);
+            // Negation in offset binary: the byte 128 - x is 256 - (128 + x).  For
+            // words whose four bytes y are all >= 1, 0x01010100 - y equals the
+            // bytes 256 - y (the borrows out of bytes 0..2 are the 1s added to
+            // bytes 1..3, and the one out of byte 3 leaves the word).
             const uint32_t Msv = spread(av[j]);
-            const uint32_t lnew = select(Msv ^ MS, kHigh - m, kHigh | m);
-            const uint32_t c = cap127(a + m);
-            const uint32_t e_same = select(Msv, kHigh - c, kHigh | c);
-            const uint32_t e_opp = select(Msv, kHigh - a + m, kHigh + a - m);
+            const uint32_t hm = kHigh | m;             // 128 + m, bytes >= 128
+            const uint32_t lnew = select(Msv ^ MS, 0x01010100u - hm, hm);
+            // y = 128 + u with E_new = sv ? -u : u, u = a - m (opposite signs,
+            // in [-127, 127]) or min(a + m, 127) (same sign); bytes >= 1
+            const uint32_t y = select(MS, kHigh + a - m, kHigh | cap127(a + m));
             uint32_t* ep = &C.E_s[idx[j]];
             const uint32_t eo = *ep;
             const uint32_t sat = spread(absdiff(eo, kHigh) + kOnes);  // |E| = 127
-            *ep = select(C.active & ~sat, select(MS, e_opp, e_same), eo);
+            *ep = select(C.active & ~sat, select(Msv, 0x01010100u - y, y), eo);
             Lp[j * Lstep] = lnew;
         }
     }
