@@ -86,7 +86,6 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
     const int d = valid ? C.d : 0;
     const int h = (d + 1) >> 1;
     const int cnt = half ? d - h : h;           // edges walked by this thread
-    const int partner = half ? h : d - h;
     const int Z = C.Z;
     const int k0 = half ? d - 1 : 0;             // first edge of the walk
     const int kdir = half ? -1 : 1;
@@ -121,13 +120,14 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
     for (int j = 0; j < HMAX; ++j) {
         if (j < cnt) {
             const uint32_t a = av[j] & kMax;
-            F[j] = (j == 0) ? a : tau(F[j >= 1 ? j - 1 : 0], a);
-            if (j == cnt - 1) tot = F[j];
+            tot = (j == 0) ? a : tau(tot, a);
+            F[j] = tot;
         }
     }
+    // A half that walks no edge sends tot = MSG_max: for a degree-1 row the one
+    // edge then gets m = MSG_max, the box-plus over the empty set.
     uint32_t R = __shfl_xor_sync(0xffffffffu, tot, W);
     S ^= __shfl_xor_sync(0xffffffffu, S, W);
-    bool rvalid = partner > 0;
     const uint32_t MS = spread(S);
 
 #pragma unroll(HMAX)
@@ -136,11 +136,8 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
         if (j < cnt) {
             const uint32_t a = av[j] & kMax;
             const uint32_t Fp = F[j >= 1 ? j - 1 : 0];
-            uint32_t m;
-            if (rvalid) m = (j == 0) ? R : tau(Fp, R);
-            else m = (j == 0) ? kMax : Fp;       // no edge beyond: left fold alone (degree 1: MSG_max)
-            if (j > 0) R = rvalid ? tau(a, R) : a;
-            rvalid = true;
+            uint32_t m = (j == 0) ? R : tau(Fp, R);
+            if (j > 0) R = tau(a, R);
             if (TABLES) m = apply_table(m, C.sq, C.oq);
             // Negation in offset binary: the byte 128 - x is 256 - (128 + x).  For
             // words whose four bytes y are all >= 1, 0x01010100 - y equals the
