@@ -5,7 +5,8 @@ Bob's keys, Alice's syndromes, the per-frame QBERs and the rate-adaptation
 counts, quantises the channel LLRs (section 3.1, with the punctured and
 shortened positions of section 4.1) and runs the layered int8 decoder
 (sections 2 and 3).  ``reconcile_host`` does the same from host buffers,
-including the host-device copies.
+including the host-device copies; ``reconcile_host_stream`` does it for a
+sequence of batches with the copies overlapped with decoding.
 """
 from __future__ import annotations
 
@@ -57,15 +58,21 @@ class Reconciler:
     def reconcile_host(self, bob_bits, syndrome, qber, max_iter, n_punct=None, n_short=None, known=None,
                        persistent=False, words=0, ctas_per_sm=0):
         """Host tensors (ideally pinned) in, host tensors out.  Returns
-        ((bits, iters, ok), h2d_bytes, d2h_bytes)."""
+        ((bits, iters, ok), h2d_bytes, d2h_bytes).  The persistent launch
+        claims frames hardest first (order computed here from the host-side
+        rate counts and QBERs)."""
         dev = self.device
+        order = None
+        if persistent and n_punct is not None and n_short is not None:
+            order = torch.from_numpy(hardest_first(n_punct.numpy(), n_short.numpy(), qber.numpy()))
         to = lambda t: None if t is None else t.to(dev, non_blocking=True)
-        d_in = [to(t) for t in (bob_bits, syndrome, qber, n_punct, n_short, known)]
-        h2d = sum(int(t.numel() * t.element_size()) for t in (bob_bits, syndrome, qber, n_punct, n_short, known)
-                  if t is not None)
+        ins = (bob_bits, syndrome, qber, n_punct, n_short, known, order)
+        d_in = [to(t) for t in ins]
+        h2d = sum(int(t.numel() * t.element_size()) for t in ins if t is not None)
         if persistent:
             bits, iters, ok = self.reconcile_persistent(d_in[0], d_in[1], d_in[2], max_iter, d_in[3], d_in[4],
-                                                        d_in[5], words=words, ctas_per_sm=ctas_per_sm)
+                                                        d_in[5], frame_list=d_in[6], words=words,
+                                                        ctas_per_sm=ctas_per_sm)
         else:
             bits, iters, ok = self.reconcile(d_in[0], d_in[1], d_in[2], max_iter, d_in[3], d_in[4], d_in[5])
         outs = []
@@ -75,6 +82,77 @@ class Reconciler:
             outs.append(h)
         d2h = sum(int(t.numel() * t.element_size()) for t in outs)
         return tuple(outs), h2d, d2h
+
+    def reconcile_host_stream(self, batches, max_iter, persistent=False, words=0, ctas_per_sm=0):
+        """``reconcile_host`` over a sequence of batches with the copies
+        overlapped with decoding.  Each batch is a tuple of host tensors
+        (ideally pinned) as for ``reconcile_host``: bob_bits, syndrome, qber
+        and optionally n_punct, n_short, known, all batches of one shape.
+
+        Two device slots alternate.  Batch k's inputs are copied in on one
+        copy stream while batch k-1 decodes; its results are copied out on a
+        second copy stream while batch k+1 decodes; CUDA events order every
+        reuse of a slot, the host never waits inside the loop.  Returns, per
+        batch, ((bits, iters, ok) host tensors, h2d_bytes, d2h_bytes); all
+        results are complete when the call returns."""
+        dev = self.device
+        comp = torch.cuda.current_stream(dev)
+        h2d_s, d2h_s = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        slots = [None, None]    # (device inputs, device outputs) per slot
+        freed = [None, None]    # slot's last decode done: its inputs may be overwritten
+        drained = [None, None]  # slot's outputs copied out: they may be overwritten
+        results = []
+        for k, batch in enumerate(batches):
+            s = k & 1
+            bob, syn, q, npn, ns, kn = (tuple(batch) + (None,) * 6)[:6]
+            order = None
+            if persistent and npn is not None and ns is not None:
+                order = torch.from_numpy(hardest_first(npn.numpy(), ns.numpy(), q.numpy())).pin_memory()
+            ins = (bob, syn, q, npn, ns, kn, order)
+            if slots[s] is None:
+                d_in = [None if t is None else torch.empty(t.shape, dtype=t.dtype, device=dev) for t in ins]
+                B = bob.shape[0]
+                d_out = (torch.empty((B, self.code.nbytes), dtype=torch.uint8, device=dev),
+                         torch.empty((B,), dtype=torch.int32, device=dev),
+                         torch.empty((B,), dtype=torch.uint8, device=dev))
+                slots[s] = (d_in, d_out)
+            d_in, d_out = slots[s]
+            with torch.cuda.stream(h2d_s):
+                if freed[s] is not None:
+                    h2d_s.wait_event(freed[s])
+                for d, h in zip(d_in, ins):
+                    if h is not None:
+                        d.copy_(h, non_blocking=True)
+                ready = torch.cuda.Event()
+                ready.record(h2d_s)
+            comp.wait_event(ready)
+            if drained[s] is not None:
+                comp.wait_event(drained[s])
+            if persistent:
+                self.reconcile_persistent(d_in[0], d_in[1], d_in[2], max_iter, d_in[3], d_in[4], d_in[5],
+                                          frame_list=d_in[6], words=words, ctas_per_sm=ctas_per_sm, out=d_out)
+            else:
+                self.reconcile(d_in[0], d_in[1], d_in[2], max_iter, d_in[3], d_in[4], d_in[5], out=d_out)
+            done = torch.cuda.Event()
+            done.record(comp)
+            freed[s] = done
+            with torch.cuda.stream(d2h_s):
+                d2h_s.wait_event(done)
+                outs = []
+                for t in d_out:
+                    h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                    h.copy_(t, non_blocking=True)
+                    outs.append(h)
+                dr = torch.cuda.Event()
+                dr.record(d2h_s)
+                drained[s] = dr
+            h2d = sum(int(t.numel() * t.element_size()) for t in ins if t is not None)
+            d2h = sum(int(t.numel() * t.element_size()) for t in outs)
+            results.append((tuple(outs), h2d, d2h))
+        d2h_s.synchronize()
+        h2d_s.synchronize()
+        comp.synchronize()
+        return results
 
 
 def hardest_first(n_punct, n_short, qber) -> np.ndarray:

@@ -76,3 +76,59 @@ def test_interactive_protocol_matches_oracle_per_round_state():
     assert np.array_equal(inputs.unpack_bits(res["bits"], n), ob)
     # frames that needed more rounds ended at a higher efficiency
     assert (res["f"][res["rounds"] > 0] > 1.1).all()
+
+
+def test_host_buffer_path_matches_oracle_and_counts_bytes():
+    """reconcile_host (pinned host buffers in and out, persistent launch in
+    hardest-first order) gives the oracle's results frame for frame."""
+    from paper_1903_10107_gb300.pipeline import Reconciler
+    B = 40
+    base, Z, n, m, q, xa, yb, tb = _code_and_frames(B, seed=13)
+    rec = Reconciler(base, Z, tb, llr_scale=SCALE)
+    p, s = rec.plan(q, 1.5)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    syn = rec.code.syndrome(torch.from_numpy(xa).cuda()).cpu()
+    (bits, iters, ok), h2d, d2h = rec.reconcile_host(pin(yb), syn.pin_memory(), pin(q), 50, pin(p), pin(s),
+                                                     pin(xa), persistent=True)
+    torch.cuda.synchronize()
+    assert h2d == yb.nbytes + syn.numel() + q.nbytes + p.nbytes + s.nbytes + xa.nbytes + 4 * B
+    assert d2h == bits.numel() + 4 * B + B
+    rank = orate.position_rank(base, Z, tb)
+    st = np.stack([orate.position_states(rank, int(p[f]), int(s[f])) for f in range(B)])
+    xa_u = inputs.unpack_bits(xa, n)
+    llr = orc.llr_frames(inputs.unpack_bits(yb, n), q, st, xa_u, scale=SCALE)
+    ob, oi, oo, _ = orc.decode(base, Z, llr, orc.syndrome(base, Z, xa_u), 50)
+    assert np.array_equal(ok.numpy(), oo) and np.array_equal(iters.numpy(), oi)
+    assert np.array_equal(inputs.unpack_bits(bits.numpy(), n), ob)
+
+
+def test_host_stream_overlapped_batches_match_oracle():
+    """Three batches through reconcile_host_stream (two device slots reused,
+    copies on their own streams) each give the oracle's results."""
+    from paper_1903_10107_gb300.pipeline import Reconciler
+    B = 24
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    cases, batches = [], []
+    rec = None
+    for seed in (21, 22, 23):
+        base, Z, n, m, q, xa, yb, tb = _code_and_frames(B, seed=5)  # one code for all batches
+        q = inputs.frame_qbers(B, 0.01, 0.08, seed)
+        xa = inputs.alice_keys(B, n, seed)
+        yb = xa ^ inputs.bsc_noise(B, n, q, seed)
+        if rec is None:
+            rec = Reconciler(base, Z, tb, llr_scale=SCALE)
+        p, s = rec.plan(q, 1.5)
+        syn = rec.code.syndrome(torch.from_numpy(xa).cuda()).cpu()
+        batches.append((pin(yb), syn.pin_memory(), pin(q), pin(p), pin(s), pin(xa)))
+        cases.append((q, xa, yb, p, s))
+    out = rec.reconcile_host_stream(batches, 50, persistent=True)
+    rank = orate.position_rank(base, Z, tb)
+    for (bits, iters, ok), h2d, d2h in out:
+        assert h2d > 0 and d2h == bits.numel() + 5 * B
+    for ((bits, iters, ok), _, _), (q, xa, yb, p, s) in zip(out, cases):
+        st = np.stack([orate.position_states(rank, int(p[f]), int(s[f])) for f in range(B)])
+        xa_u = inputs.unpack_bits(xa, n)
+        llr = orc.llr_frames(inputs.unpack_bits(yb, n), q, st, xa_u, scale=SCALE)
+        ob, oi, oo, _ = orc.decode(base, Z, llr, orc.syndrome(base, Z, xa_u), 50)
+        assert np.array_equal(ok.numpy(), oo) and np.array_equal(iters.numpy(), oi)
+        assert np.array_equal(inputs.unpack_bits(bits.numpy(), n), ob)
