@@ -164,4 +164,4 @@ def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma, kappa=1.0):
     sgn = torch.tensor(1.0 - 2.0 * np.asarray(xa, dtype=np.float64))
     loss = torch.nn.functional.softplus(-sgn * E).mean()
     loss.backward()
-    return float(loss), al.grad.numpy().copy(), ga.grad.numpy().copy(), E.detach().numpy()
+    return float(loss.detach()), al.grad.numpy().copy(), ga.grad.numpy().copy(), E.detach().numpy()

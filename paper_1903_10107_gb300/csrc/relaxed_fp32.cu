@@ -13,7 +13,7 @@
 // The variable-node update is the plain Eq. 9; the loss is the mean binary
 // cross entropy of the final soft values against Alice's bits.
 //
-// Work decomposition: a CTA holds FR frames, one thread per (frame, check
+// Work decomposition: a CTA holds FR frames, two threads per (frame, check
 // row).  Soft values live in shared memory; the forward writes iteration-
 // boundary checkpoints of E and L to global memory.  The adjoint walks the
 // iterations backwards; for each it recomputes that iteration's forward from
@@ -32,6 +32,12 @@ __device__ __forceinline__ float bplus(float x, float y, float kap, float ikap) 
 }
 
 __device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
 
 // d beta_k / dx = s((x+y)/k) - s((x-y)/k), and symmetrically for y.
 __device__ __forceinline__ void bplus_grad(float x, float y, float ikap, float& dx, float& dy) {
@@ -68,43 +74,71 @@ __device__ __forceinline__ float syn_sign(const RelaxArgs& A, int64_t f, int c) 
     return ((A.syn[f * mbytes + (c >> 3)] >> (c & 7)) & 1) ? -1.0f : 1.0f;
 }
 
+// Two threads share a check row, as in the integer decoder: half 0 walks the
+// row's edges upward from the first, half 1 downward from the last.  Each
+// folds beta over its own walk (beta is symmetric, so half 1's fold is the
+// right fold B of the forward-backward scheme), the halves swap their fold
+// totals and sign products with one shuffle each, and each walks back,
+// extending the partner's total through its own edges, to form every
+//     m_k = beta(F_{k-1}, B_{k+1})            (Eq. 7, forward-backward).
+// beta is bitwise symmetric in FP32 (min, x + y and |x - y| do not depend on
+// the order of the operands), so every value equals the one a single thread
+// folding the whole row computes.  A half that walks no edge sends the
+// empty box-plus, which is what the one edge of a degree-1 row receives.
+//
+// Per-thread state: own fold O[j] after slot j, and (adjoint) the partner
+// chain beyond slot j, X[j] = B_{k+1} or F_{k-1} for the slot's edge k.
+struct RowHalf {
+    int cnt, k0, kdir;
+};
+
+__device__ __forceinline__ RowHalf row_half(int d, int half) {
+    const int h = (d + 1) >> 1;
+    return RowHalf{half ? d - h : h, half ? d - 1 : 0, half ? -1 : 1};
+}
+
 // Forward of one check row; Lold == nullptr means the messages are 0.
-template <int DMAX>
+// `d` is 0 for a thread without a row (it still joins the shuffles).
+template <int HMAX>
 __device__ __forceinline__ void row_forward(float* E, const float* Lold, float* Lnew, float* Vout, const int2* et,
-                                            int d, int r, int Z, float S, float al, float ga, float kap,
+                                            int d, int half, int r, int Z, float S, float al, float ga, float kap,
                                             float ikap) {
-    float v[DMAX], a[DMAX], F[DMAX];
-    int idx[DMAX];
-#pragma unroll(DMAX)
-    for (int k = 0; k < DMAX; ++k) {
-        if (k < d) {
+    const RowHalf H = row_half(d, half);
+    float v[HMAX], O[HMAX];
+    int idx[HMAX];
+    float sgn = 1.0f;
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < H.cnt) {
+            const int k = H.k0 + j * H.kdir;
             const int2 t = et[k];
-            idx[k] = t.x + ldpc_dev::wrap(r + t.y, Z);
-            v[k] = E[idx[k]] - (Lold ? Lold[(size_t)k * Z] : 0.0f);  // Eq. 8
-            a[k] = fabsf(v[k]);
-            if (v[k] < 0.0f) S = -S;                                  // Eq. 1
-            if (Vout) Vout[(size_t)k * Z] = v[k];
+            idx[j] = t.x + ldpc_dev::wrap(r + t.y, Z);
+            v[j] = E[idx[j]] - (Lold ? Lold[(size_t)k * Z] : 0.0f);  // Eq. 8
+            if (v[j] < 0.0f) sgn = -sgn;                              // Eq. 1
+            if (Vout) Vout[(size_t)k * Z] = v[j];
         }
     }
-    F[0] = a[0];
-#pragma unroll(DMAX)
-    for (int k = 1; k < DMAX - 1; ++k)
-        if (k <= d - 2) F[k] = bplus(F[k - 1], a[k], kap, ikap);
-    float R = 0.0f;
-#pragma unroll(DMAX)
-    for (int kk = 0; kk < DMAX; ++kk) {
-        const int k = DMAX - 1 - kk;
-        if (k < d) {
-            float B;
-            if (d == 1) B = kEmpty;
-            else if (k == d - 1) B = F[k >= 1 ? k - 1 : 0];
-            else if (k == 0) B = R;
-            else B = bplus(F[k >= 1 ? k - 1 : 0], R, kap, ikap);
-            if (k == d - 1) R = a[k];
-            else if (k > 0) R = bplus(a[k], R, kap, ikap);
+    float tot = kEmpty;
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < H.cnt) {
+            const float a = fabsf(v[j]);
+            tot = (j == 0) ? a : bplus(tot, a, kap, ikap);
+            O[j] = tot;
+        }
+    }
+    float X = __shfl_xor_sync(0xffffffffu, tot, 1);
+    S *= sgn * __shfl_xor_sync(0xffffffffu, sgn, 1);
+#pragma unroll(HMAX)
+    for (int jj = 0; jj < HMAX; ++jj) {
+        const int j = HMAX - 1 - jj;
+        if (j < H.cnt) {
+            const int k = H.k0 + j * H.kdir;
+            const float B = (j == 0) ? X : bplus(O[j >= 1 ? j - 1 : 0], X, kap, ikap);
+            if (j > 0) X = bplus(fabsf(v[j]), X, kap, ikap);
             const float mag = al * fmaxf(B - ga, 0.0f);
-            const float Ln = (v[k] < 0.0f ? -S : S) * mag;  // own sign removed
-            E[idx[k]] = v[k] + Ln;                          // Eq. 9
+            const float Ln = (v[j] < 0.0f ? -S : S) * mag;  // own sign removed
+            E[idx[j]] = v[j] + Ln;                          // Eq. 9
             if (Lnew) Lnew[(size_t)k * Z] = Ln;
         }
     }
@@ -113,223 +147,291 @@ __device__ __forceinline__ void row_forward(float* E, const float* Lold, float* 
 // Adjoint of one check row.  G holds the adjoint of E after the layer and
 // receives the adjoint before it; gLrow holds the adjoint of the new messages
 // and receives the adjoint of the old ones.
-template <int DMAX>
+template <int HMAX>
 __device__ __forceinline__ void row_backward(float* G, const float* Vrow, float* gLrow, const int2* et, int d,
-                                             int r, int Z, float S, float al, float ga, float kap, float ikap,
-                                             float& acc_a, float& acc_g) {
-    float a[DMAX], sg[DMAX], F[DMAX], Rr[DMAX], gF[DMAX], gR[DMAX], gA[DMAX], gE[DMAX], gB[DMAX];
-    int idx[DMAX];
-#pragma unroll(DMAX)
-    for (int k = 0; k < DMAX; ++k) {
-        if (k < d) {
+                                             int dtrue, int half, int r, int Z, float S, float al, float ga,
+                                             float kap, float ikap, float& acc_a, float& acc_g) {
+    const RowHalf H = row_half(d, half);
+    float a[HMAX], O[HMAX], X[HMAX], gO[HMAX], gX[HMAX], gA[HMAX];
+    int idx[HMAX];
+    uint32_t neg = 0;  // bit j: v_j < 0
+    float sgn = 1.0f;
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < H.cnt) {
+            const int k = H.k0 + j * H.kdir;
             const int2 t = et[k];
-            idx[k] = t.x + ldpc_dev::wrap(r + t.y, Z);
+            idx[j] = t.x + ldpc_dev::wrap(r + t.y, Z);
             const float v = Vrow[(size_t)k * Z];
-            a[k] = fabsf(v);
-            sg[k] = v < 0.0f ? -1.0f : 1.0f;
-            S *= sg[k];
-            gF[k] = gR[k] = gA[k] = 0.0f;
+            a[j] = fabsf(v);
+            if (v < 0.0f) {
+                neg |= 1u << j;
+                sgn = -sgn;
+            }
+            gO[j] = gX[j] = gA[j] = 0.0f;
         }
     }
-    F[0] = a[0];
-#pragma unroll(DMAX)
-    for (int k = 1; k < DMAX - 1; ++k)
-        if (k <= d - 2) F[k] = bplus(F[k - 1], a[k], kap, ikap);
-#pragma unroll(DMAX)
-    for (int kk = 0; kk < DMAX; ++kk) {
-        const int k = DMAX - 1 - kk;
-        if (k < d) {
-            if (k == d - 1) Rr[k] = a[k];
-            else if (k >= 1) Rr[k] = bplus(a[k], Rr[k + 1 < DMAX ? k + 1 : 0], kap, ikap);
+    float tot = kEmpty;
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < H.cnt) {
+            tot = (j == 0) ? a[j] : bplus(tot, a[j], kap, ikap);
+            O[j] = tot;
         }
     }
-    // magnitudes and their adjoints
-#pragma unroll(DMAX)
-    for (int k = 0; k < DMAX; ++k) {
-        if (k < d) {
-            float B;
-            if (d == 1) B = kEmpty;
-            else if (k == 0) B = Rr[1 < DMAX ? 1 : 0];
-            else if (k == d - 1) B = F[k - 1 >= 0 ? k - 1 : 0];
-            else B = bplus(F[k - 1 >= 0 ? k - 1 : 0], Rr[k + 1 < DMAX ? k + 1 : 0], kap, ikap);
-            gE[k] = G[idx[k]];
-            const float gtot = gLrow[(size_t)k * Z] + gE[k];  // L_new feeds E (Eq. 9) and the next iteration
-            const float gmag = gtot * S * sg[k];
+    float x = __shfl_xor_sync(0xffffffffu, tot, 1);
+    S *= sgn * __shfl_xor_sync(0xffffffffu, sgn, 1);
+#pragma unroll(HMAX)
+    for (int jj = 0; jj < HMAX; ++jj) {  // partner chain beyond every slot
+        const int j = HMAX - 1 - jj;
+        if (j < H.cnt) {
+            X[j] = x;
+            if (j > 0) x = bplus(a[j], x, kap, ikap);
+        }
+    }
+    // magnitudes, their adjoints, and the adjoint through m_j = beta(O_{j-1}, X_j)
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < H.cnt) {
+            const int k = H.k0 + j * H.kdir;
+            const float B = (j == 0) ? X[0] : bplus(O[j >= 1 ? j - 1 : 0], X[j], kap, ikap);
+            const float sj = ((neg >> j) & 1u) ? -S : S;
+            const float gtot = gLrow[(size_t)k * Z] + G[idx[j]];  // L_new feeds E (Eq. 9) and the next iteration
+            const float gmag = gtot * sj;
             const bool pos = B > ga;
             acc_a += gmag * fmaxf(B - ga, 0.0f);
             acc_g -= pos ? gmag * al : 0.0f;
-            gB[k] = (pos && d > 1) ? gmag * al : 0.0f;
-        }
-    }
-    // through m_k = beta(F_{k-1}, B_{k+1})
-#pragma unroll(DMAX)
-    for (int k = 0; k < DMAX; ++k) {
-        if (k < d && d > 1) {
-            if (k == 0) gR[1 < DMAX ? 1 : 0] += gB[k];
-            else if (k == d - 1) gF[k - 1 >= 0 ? k - 1 : 0] += gB[k];
-            else {
+            const float gm = (pos && dtrue > 1) ? gmag * al : 0.0f;
+            if (j == 0) {
+                gX[0] += gm;
+            } else {
                 float dx, dy;
-                bplus_grad(F[k - 1 >= 0 ? k - 1 : 0], Rr[k + 1 < DMAX ? k + 1 : 0], ikap, dx, dy);
-                gF[k - 1 >= 0 ? k - 1 : 0] += gB[k] * dx;
-                gR[k + 1 < DMAX ? k + 1 : 0] += gB[k] * dy;
+                bplus_grad(O[j >= 1 ? j - 1 : 0], X[j], ikap, dx, dy);
+                gO[j >= 1 ? j - 1 : 0] += gm * dx;
+                gX[j] += gm * dy;
             }
         }
     }
-    // right chain R_k = beta(a_k, R_{k+1}), k = 1 .. d-2, then R_{d-1} = a_{d-1}
-#pragma unroll(DMAX)
-    for (int k = 1; k < DMAX; ++k) {
-        if (k < d) {
-            if (k <= d - 2) {
+    // partner chain X_{j-1} = beta(a_j, X_j), ascending: the adjoint that
+    // reaches the far end belongs to the partner's fold total
+    float g = 0.0f;
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < H.cnt) {
+            if (j == 0) {
+                g = gX[0];
+            } else {
                 float dx, dy;
-                bplus_grad(a[k], Rr[k + 1 < DMAX ? k + 1 : 0], ikap, dx, dy);
-                gA[k] += gR[k] * dx;
-                gR[k + 1 < DMAX ? k + 1 : 0] += gR[k] * dy;
-            } else if (k == d - 1) {
-                gA[k] += gR[k];
+                bplus_grad(a[j], X[j], ikap, dx, dy);
+                gA[j] += g * dx;
+                g = gX[j] + g * dy;
             }
         }
     }
-    // left chain F_k = beta(F_{k-1}, a_k), k = d-2 .. 1, then F_0 = a_0
-#pragma unroll(DMAX)
-    for (int kk = 0; kk < DMAX; ++kk) {
-        const int k = DMAX - 1 - kk;
-        if (k >= 1 && k <= d - 2) {
-            float dx, dy;
-            bplus_grad(F[k - 1 >= 0 ? k - 1 : 0], a[k], ikap, dx, dy);
-            gF[k - 1 >= 0 ? k - 1 : 0] += gF[k] * dx;
-            gA[k] += gF[k] * dy;
+    // own fold O_j = beta(O_{j-1}, a_j), descending, starting from the
+    // adjoint of the total that the partner's chain sends back
+    float go = __shfl_xor_sync(0xffffffffu, g, 1);
+#pragma unroll(HMAX)
+    for (int jj = 0; jj < HMAX; ++jj) {
+        const int j = HMAX - 1 - jj;
+        if (j < H.cnt) {
+            go += gO[j];
+            if (j > 0) {
+                float dx, dy;
+                bplus_grad(O[j >= 1 ? j - 1 : 0], a[j], ikap, dx, dy);
+                gA[j] += go * dy;
+                go *= dx;
+            } else {
+                gA[0] += go;
+            }
         }
     }
-    if (d > 1) gA[0] += gF[0];
-#pragma unroll(DMAX)
-    for (int k = 0; k < DMAX; ++k) {
-        if (k < d) {
-            const float gv = gE[k] + gA[k] * sg[k];  // d|v|/dv = sign(v)
-            G[idx[k]] = gv;                           // adjoint of E before the layer
-            gLrow[(size_t)k * Z] = -gv;               // adjoint of the old message (Eq. 8)
+#pragma unroll(HMAX)
+    for (int j = 0; j < HMAX; ++j) {
+        if (j < H.cnt) {
+            const int k = H.k0 + j * H.kdir;
+            const float gv = G[idx[j]] + gA[j] * (((neg >> j) & 1u) ? -1.0f : 1.0f);  // d|v|/dv = sign(v)
+            G[idx[j]] = gv;                                                           // adjoint of E before the layer
+            gLrow[(size_t)k * Z] = -gv;                                               // adjoint of the old message (Eq. 8)
         }
     }
 }
 
-template <int DMAX>
+// CTA shape: FR frames, two threads per check row; RT rows of a frame per
+// pass (RT = Z unless 2 Z FR exceeds the block, then passes over the rows).
+struct Shape {
+    int FR, RT, T;
+};
+
+__host__ __device__ inline Shape cta_shape(int Z) {
+    int fr = 512 / (2 * Z);
+    fr = fr < 1 ? 1 : (fr > 4 ? 4 : fr);
+    const int rt = 2 * Z * fr <= 512 ? Z : 256;
+    const int t = ((2 * rt * fr + 31) / 32) * 32;
+    return Shape{fr, rt, t};
+}
+
+template <int HMAX>
 __global__ void __launch_bounds__(512) relaxed_forward_kernel(RelaxArgs A) {
     extern __shared__ __align__(16) float fsm[];
-    const int Z = A.Z, n = A.n, T = blockDim.x, FR = T / Z;
-    const int tid = threadIdx.x, fl = tid / Z, r = tid - fl * Z;
+    const int Z = A.Z, n = A.n;
+    const Shape sh = cta_shape(Z);
+    const int FR = sh.FR, RT = sh.RT, T = blockDim.x;
+    const int tid = threadIdx.x, half = tid & 1, q = tid >> 1;
+    const int flq = q / RT, rr = q - flq * RT;
+    const int fl = flq < FR ? flq : 0;
     float* E_s = fsm;
     int32_t* s_tab = reinterpret_cast<int32_t*>(fsm + (size_t)FR * n);
     const ldpc_dev::Tables TB = ldpc_dev::load_tables(s_tab, A.tab, A.Mb, A.nblk, Z, 1, tid, T);
-    const int64_t f = (int64_t)blockIdx.x * FR + fl;
-    const bool valid = f < A.batch;
-    float* E = E_s + (size_t)fl * n;
-    if (valid)
-        for (int j = r; j < n; j += Z) E[j] = A.llr[f * n + j];
+    const int64_t fbase = (int64_t)blockIdx.x * FR;
+    const int64_t f = fbase + fl;
+    const bool valid = flq < FR && f < A.batch;
+    for (int i = tid; i < FR * n; i += T) {
+        const int64_t ff = fbase + i / n;
+        if (ff < A.batch) E_s[i] = A.llr[ff * n + i % n];
+    }
     __syncthreads();
+    float* E = E_s + (size_t)fl * n;
     const float kap = A.kappa, ikap = 1.0f / A.kappa;
     for (int t = 0; t < A.iters; ++t) {
-        if (valid)
-            for (int j = r; j < n; j += Z) A.ckE[((int64_t)t * A.batch + f) * n + j] = E[j];
+        for (int i = tid; i < FR * n; i += T) {
+            const int64_t ff = fbase + i / n;
+            if (ff < A.batch) A.ckE[((int64_t)t * A.batch + ff) * n + i % n] = E_s[i];
+        }
         const float* Lold = t > 0 ? A.ckL + ((int64_t)t * A.batch + f) * A.edges : nullptr;
         float* Lnew = t + 1 < A.iters ? A.ckL + ((int64_t)(t + 1) * A.batch + f) * A.edges : nullptr;
         for (int i = 0; i < A.Mb; ++i) {
             const int d = TB.deg[i], b0 = TB.off[i];
-            if (valid && d > 0) {
+            if (d > 0) {
                 const int c = A.cls[i];
-                const size_t e0 = (size_t)b0 * Z + r;
-                row_forward<DMAX>(E, Lold ? Lold + e0 : nullptr, Lnew ? Lnew + e0 : nullptr, nullptr, TB.et + b0, d,
-                                  r, Z, syn_sign(A, f, i * Z + r), A.alpha[t * A.ncls + c], A.gamma[t * A.ncls + c],
-                                  kap, ikap);
+                for (int r0 = 0; r0 < Z; r0 += RT) {
+                    const int r = r0 + rr;
+                    const bool ok = valid && r < Z;
+                    const int rs = ok ? r : 0;
+                    const size_t e0 = (size_t)b0 * Z + rs;
+                    row_forward<HMAX>(E, Lold ? Lold + e0 : nullptr, Lnew ? Lnew + e0 : nullptr, nullptr,
+                                      TB.et + b0, ok ? d : 0, half, rs, Z, ok ? syn_sign(A, f, i * Z + rs) : 1.0f,
+                                      A.alpha[t * A.ncls + c], A.gamma[t * A.ncls + c], kap, ikap);
+                }
             }
             __syncthreads();
         }
     }
-    if (valid) {
-        const int nbytes = (n + 7) / 8;
-        float part = 0.0f;
-        for (int j = r; j < n; j += Z) {
-            const float e = E[j];
-            A.ckE[((int64_t)A.iters * A.batch + f) * n + j] = e;
-            if (A.bits && A.loss) {
-                const float sgn = ((A.bits[f * nbytes + (j >> 3)] >> (j & 7)) & 1) ? -1.0f : 1.0f;
-                const float z = -sgn * e;  // BCE with logit e for bit 0: softplus(-(1-2x) e)
-                part += fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));
-            }
+    const int nbytes = (n + 7) / 8;
+    float part = 0.0f;
+    for (int i = tid; i < FR * n; i += T) {
+        const int64_t ff = fbase + i / n;
+        if (ff >= A.batch) continue;
+        const int j = i % n;
+        const float e = E_s[i];
+        A.ckE[((int64_t)A.iters * A.batch + ff) * n + j] = e;
+        if (A.bits && A.loss) {
+            const float sgn = ((A.bits[ff * nbytes + (j >> 3)] >> (j & 7)) & 1) ? -1.0f : 1.0f;
+            const float z = -sgn * e;  // BCE with logit e for bit 0: softplus(-(1-2x) e)
+            part += fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));
         }
-        if (A.bits && A.loss) atomicAdd(A.loss, part / ((float)A.batch * (float)n));
+    }
+    if (A.bits && A.loss) {
+        part = warp_sum(part);
+        if ((tid & 31) == 0) atomicAdd(A.loss, part / ((float)A.batch * (float)n));
     }
 }
 
-template <int DMAX>
+template <int HMAX>
 __global__ void __launch_bounds__(512) relaxed_backward_kernel(RelaxArgs A) {
     extern __shared__ __align__(16) float fsm[];
-    const int Z = A.Z, n = A.n, T = blockDim.x, FR = T / Z;
-    const int tid = threadIdx.x, fl = tid / Z, r = tid - fl * Z;
+    const int Z = A.Z, n = A.n;
+    const Shape sh = cta_shape(Z);
+    const int FR = sh.FR, RT = sh.RT, T = blockDim.x;
+    const int tid = threadIdx.x, half = tid & 1, q = tid >> 1;
+    const int flq = q / RT, rr = q - flq * RT;
+    const int fl = flq < FR ? flq : 0;
     float* E_s = fsm;
     float* G_s = fsm + (size_t)FR * n;
     float* s_acc = G_s + (size_t)FR * n;  // [2 * ncls]
     int32_t* s_tab = reinterpret_cast<int32_t*>(s_acc + 2 * A.ncls);
     const ldpc_dev::Tables TB = ldpc_dev::load_tables(s_tab, A.tab, A.Mb, A.nblk, Z, 1, tid, T);
-    const int64_t f = (int64_t)blockIdx.x * FR + fl;
-    const bool valid = f < A.batch;
-    float* E = E_s + (size_t)fl * n;
+    const int64_t fbase = (int64_t)blockIdx.x * FR;
+    const int64_t f = fbase + fl;
+    const bool valid = flq < FR && f < A.batch;
     float* G = G_s + (size_t)fl * n;
+    float* E = E_s + (size_t)fl * n;
     const int nbytes = (n + 7) / 8;
     const float kap = A.kappa, ikap = 1.0f / A.kappa;
-    if (valid) {
-        const float inv = 1.0f / ((float)A.batch * (float)n);
-        for (int j = r; j < n; j += Z) {
-            const float e = A.ckE[((int64_t)A.iters * A.batch + f) * n + j];
-            const float sgn = ((A.bits[f * nbytes + (j >> 3)] >> (j & 7)) & 1) ? -1.0f : 1.0f;
-            G[j] = -sgn * sigm(-sgn * e) * inv;  // d softplus(-sgn e) / de
-        }
-        float* gl = A.gL + f * A.edges;
-        for (int64_t e = r; e < A.edges; e += Z) gl[e] = 0.0f;  // the last messages feed nothing
+    const float inv = 1.0f / ((float)A.batch * (float)n);
+    for (int i = tid; i < FR * n; i += T) {
+        const int64_t ff = fbase + i / n;
+        if (ff >= A.batch) continue;
+        const int j = i % n;
+        const float e = A.ckE[((int64_t)A.iters * A.batch + ff) * n + j];
+        const float sgn = ((A.bits[ff * nbytes + (j >> 3)] >> (j & 7)) & 1) ? -1.0f : 1.0f;
+        G_s[i] = -sgn * sigm(-sgn * e) * inv;  // d softplus(-sgn e) / de
+    }
+    for (int64_t i = tid; i < (int64_t)FR * A.edges; i += T) {  // the last messages feed nothing
+        const int64_t ff = fbase + i / A.edges;
+        if (ff < A.batch) A.gL[ff * A.edges + i % A.edges] = 0.0f;
     }
     for (int t = A.iters - 1; t >= 0; --t) {
-        if (valid)
-            for (int j = r; j < n; j += Z) E[j] = A.ckE[((int64_t)t * A.batch + f) * n + j];
-        for (int q = tid; q < 2 * A.ncls; q += T) s_acc[q] = 0.0f;
+        for (int i = tid; i < FR * n; i += T) {
+            const int64_t ff = fbase + i / n;
+            if (ff < A.batch) E_s[i] = A.ckE[((int64_t)t * A.batch + ff) * n + i % n];
+        }
+        for (int qq = tid; qq < 2 * A.ncls; qq += T) s_acc[qq] = 0.0f;
         __syncthreads();
         const float* Lold = t > 0 ? A.ckL + ((int64_t)t * A.batch + f) * A.edges : nullptr;
         float* Vf = A.V + f * A.edges;
         for (int i = 0; i < A.Mb; ++i) {  // recompute iteration t, keeping L_ji
             const int d = TB.deg[i], b0 = TB.off[i];
-            if (valid && d > 0) {
+            if (d > 0) {
                 const int c = A.cls[i];
-                const size_t e0 = (size_t)b0 * Z + r;
-                row_forward<DMAX>(E, Lold ? Lold + e0 : nullptr, nullptr, Vf + e0, TB.et + b0, d, r, Z,
-                                  syn_sign(A, f, i * Z + r), A.alpha[t * A.ncls + c], A.gamma[t * A.ncls + c], kap,
-                                  ikap);
+                for (int r0 = 0; r0 < Z; r0 += RT) {
+                    const int r = r0 + rr;
+                    const bool ok = valid && r < Z;
+                    const int rs = ok ? r : 0;
+                    const size_t e0 = (size_t)b0 * Z + rs;
+                    row_forward<HMAX>(E, Lold ? Lold + e0 : nullptr, nullptr, Vf + e0, TB.et + b0, ok ? d : 0, half,
+                                      rs, Z, ok ? syn_sign(A, f, i * Z + rs) : 1.0f, A.alpha[t * A.ncls + c],
+                                      A.gamma[t * A.ncls + c], kap, ikap);
+                }
             }
             __syncthreads();
         }
         for (int i = A.Mb - 1; i >= 0; --i) {  // reverse the layers
             const int d = TB.deg[i], b0 = TB.off[i];
-            if (valid && d > 0) {
+            if (d > 0) {
                 const int c = A.cls[i];
-                const size_t e0 = (size_t)b0 * Z + r;
                 float acc_a = 0.0f, acc_g = 0.0f;
-                row_backward<DMAX>(G, Vf + e0, A.gL + f * A.edges + e0, TB.et + b0, d, r, Z,
-                                   syn_sign(A, f, i * Z + r), A.alpha[t * A.ncls + c], A.gamma[t * A.ncls + c], kap,
-                                   ikap, acc_a, acc_g);
-                atomicAdd(&s_acc[c], acc_a);
-                atomicAdd(&s_acc[A.ncls + c], acc_g);
+                for (int r0 = 0; r0 < Z; r0 += RT) {
+                    const int r = r0 + rr;
+                    const bool ok = valid && r < Z;
+                    const int rs = ok ? r : 0;
+                    const size_t e0 = (size_t)b0 * Z + rs;
+                    row_backward<HMAX>(G, Vf + e0, A.gL + f * A.edges + e0, TB.et + b0, ok ? d : 0, d, half, rs, Z,
+                                       ok ? syn_sign(A, f, i * Z + rs) : 1.0f, A.alpha[t * A.ncls + c],
+                                       A.gamma[t * A.ncls + c], kap, ikap, acc_a, acc_g);
+                }
+                // every lane of a warp works on this layer, whose class is c:
+                // sum over the warp first, one shared atomic per warp
+                acc_a = warp_sum(acc_a);
+                acc_g = warp_sum(acc_g);
+                if ((tid & 31) == 0) {
+                    atomicAdd(&s_acc[c], acc_a);
+                    atomicAdd(&s_acc[A.ncls + c], acc_g);
+                }
             }
             __syncthreads();
         }
-        for (int q = tid; q < A.ncls; q += T) {
-            atomicAdd(&A.g_alpha[t * A.ncls + q], s_acc[q]);
-            atomicAdd(&A.g_gamma[t * A.ncls + q], s_acc[A.ncls + q]);
+        for (int qq = tid; qq < A.ncls; qq += T) {
+            atomicAdd(&A.g_alpha[t * A.ncls + qq], s_acc[qq]);
+            atomicAdd(&A.g_gamma[t * A.ncls + qq], s_acc[A.ncls + qq]);
         }
         __syncthreads();
     }
-    if (valid && A.g_llr)
-        for (int j = r; j < n; j += Z) A.g_llr[f * n + j] = G[j];
-}
-
-int frames_per_cta(int Z) {
-    int fr = 512 / Z;
-    return fr < 1 ? 1 : (fr > 4 ? 4 : fr);
+    if (A.g_llr)
+        for (int i = tid; i < FR * n; i += T) {
+            const int64_t ff = fbase + i / n;
+            if (ff < A.batch) A.g_llr[ff * n + i % n] = G_s[i];
+        }
 }
 
 size_t tab_bytes(const ldpc_code* c) {
@@ -363,15 +465,16 @@ int ldpc_relaxed_forward(const ldpc_code* code, const float* llr, const uint8_t*
     if (loss && !bits) return fail(LDPC_EINVAL, "relaxed forward: the loss needs Alice's bits");
     cudaStream_t st = (cudaStream_t)stream;
     if (loss) LDPC_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
-    const int FR = frames_per_cta(c->Z);
+    const Shape sh = cta_shape(c->Z);
+    const int FR = sh.FR;
     const size_t smem = sizeof(float) * (size_t)FR * c->n + tab_bytes(c);
     if ((int64_t)smem > ldpc::max_dyn_smem(c->device)) return fail(LDPC_EUNSUPPORTED, "relaxed forward: shared memory");
     RelaxArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, c->edges, llr, syn, bits, batch, iters, alpha, gamma,
                 layer_class, n_classes, kappa, ckE, ckL, loss, nullptr, nullptr, nullptr, nullptr, nullptr};
     const int grid = (batch + FR - 1) / FR;
-    auto kern = c->max_deg <= 24 ? relaxed_forward_kernel<24> : relaxed_forward_kernel<32>;
+    auto kern = c->max_deg <= 24 ? relaxed_forward_kernel<12> : relaxed_forward_kernel<16>;
     LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, c->Z * FR, smem, st>>>(A);
+    kern<<<grid, sh.T, smem, st>>>(A);
     ldpc::count_launch();
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
@@ -392,7 +495,8 @@ int ldpc_relaxed_backward(const ldpc_code* code, const uint8_t* syn, const uint8
     if (batch == 0) return LDPC_OK;
     if (!syn || !bits || !alpha || !gamma || !layer_class || !ckE || (!ckL && iters > 1) || !V || !gL)
         return fail(LDPC_EINVAL, "relaxed backward: NULL buffer");
-    const int FR = frames_per_cta(c->Z);
+    const Shape sh = cta_shape(c->Z);
+    const int FR = sh.FR;
     const size_t smem = sizeof(float) * (2 * (size_t)FR * c->n + 2 * (size_t)n_classes) + tab_bytes(c);
     if ((int64_t)smem > ldpc::max_dyn_smem(c->device))
         return fail(LDPC_EUNSUPPORTED, "relaxed backward: shared memory");
@@ -400,9 +504,9 @@ int ldpc_relaxed_backward(const ldpc_code* code, const uint8_t* syn, const uint8
                 gamma, layer_class, n_classes, kappa, const_cast<float*>(ckE), const_cast<float*>(ckL), nullptr,
                 V, gL, grad_alpha, grad_gamma, grad_llr};
     const int grid = (batch + FR - 1) / FR;
-    auto kern = c->max_deg <= 24 ? relaxed_backward_kernel<24> : relaxed_backward_kernel<32>;
+    auto kern = c->max_deg <= 24 ? relaxed_backward_kernel<12> : relaxed_backward_kernel<16>;
     LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, c->Z * FR, smem, st>>>(A);
+    kern<<<grid, sh.T, smem, st>>>(A);
     ldpc::count_launch();
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;

@@ -98,3 +98,43 @@ def test_identity_tables_round_to_plain_decoder():
     m = RelaxedDecoder(code, 20)
     sq, oq = m.integer_tables(8.0)
     assert sq.shape == (20, w.Mb) and (sq == 16).all() and (oq == 0).all()
+
+
+def _special_rows_case(Z=16, B=6, seed=7, mu=2.0, sigma=1.5):
+    """Rows of degree 1, 2, 0, 12 and 5: the empty box-plus, a pair, an
+    empty row, a long row split unevenly between the two threads of a row."""
+    g = np.random.default_rng(seed)
+    Nb = 12
+    base = np.full((5, Nb), -1, dtype=np.int32)
+    for row, cols in ((0, [3]), (1, [0, 7]), (3, list(range(Nb))), (4, [1, 2, 5, 8, 11])):
+        base[row, cols] = g.integers(0, Z, size=len(cols))
+    n = Nb * Z
+    xa = g.integers(0, 2, size=(B, n)).astype(np.uint8)
+    from oracle import core as orc
+    syn = orc.syndrome(base, Z, xa)
+    llr = ((1 - 2.0 * xa) * mu + g.normal(0, sigma, size=(B, n))).astype(np.float32)
+    return base, Z, llr, syn, xa
+
+
+@pytest.mark.parametrize("case", ["special_rows", "z300_row_passes"])
+def test_forward_and_gradient_on_special_shapes(case):
+    if case == "special_rows":
+        base, Z, llr, syn, xa = _special_rows_case()
+        T = 4
+    else:  # two threads per row exceed one block: each thread takes two rows per layer
+        base, Z, llr, syn, xa = _case(Mb=3, Nb=8, Z=300, B=3, seed=9)
+        T = 2
+    C = len(rx.degree_classes(base)[1])
+    g = np.random.default_rng(4)
+    al = g.uniform(0.7, 1.1, (T, C)).astype(np.float32).astype(np.float64)
+    ga = g.uniform(0.05, 0.3, (T, C)).astype(np.float32).astype(np.float64)
+    kappa = 0.6
+    loss, E, g_al, g_ga, _, _ = _gpu(base, Z, llr, syn, xa, al, ga, kappa, T)
+    E64 = rx.decode(base, Z, llr.astype(np.float64), syn, T, al, ga, kappa=kappa)
+    rel = np.abs(E - E64) / np.maximum(np.abs(E64), 1.0)
+    assert rel.max() <= 1e-4, rel.max()
+    l64, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=kappa)
+    assert abs(loss - l64) <= 1e-4 * abs(l64)
+    ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
+    got = np.concatenate([g_al.ravel(), g_ga.ravel()])
+    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
