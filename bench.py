@@ -147,7 +147,8 @@ def peaks():
 
 def kernel_sources_sha():
     h = hashlib.sha256()
-    for fn in ("decode_int8.cu", "decode_persistent.cu", "row_update.cuh", "common.cuh"):
+    for fn in ("decode_int8.cu", "decode_int8.cuh", "decode_persistent.cu", "decode_persistent.cuh", "maxh.cuh",
+               "row_update.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1903_10107_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -2,13 +2,18 @@
 
 Each translation unit is compiled by its own ``nvcc -c`` in parallel and the
 objects are linked with ``nvcc -shared``; nothing is rebuilt when the library
-is newer than every source and header.
+is newer than every source and header.  Besides ``csrc/*.cu`` the build
+writes one small translation unit per unroll width listed in
+``csrc/maxh.cuh`` (``_build/gen/maxh_<width>.cu``), each instantiating the
+batch and the persistent decoder of that width, so that the many kernel
+instances compile in parallel.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
 import os
+import re
 import shutil
 import subprocess
 
@@ -30,12 +35,48 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the decoder")
 
 
+GEN_DIR = os.path.join(OUT_DIR, "gen")
+_GEN_TEMPLATE = """// Written by build.py: the batch and persistent decoders of unroll width {m}.
+#include "decode_persistent.cuh"
+
+template int ldpc_dec::decode_launch<{m}>(const ldpc_code*, const ldpc_dec::DecodeArgs&, int, int, bool,
+                                          cudaStream_t);
+template int ldpc_dec::persist_launch<{m}>(const ldpc_code*, const ldpc_dec::PersistArgs&, int, int, int*, bool,
+                                           cudaStream_t);
+"""
+
+
+def unroll_widths():
+    """The widths of LDPC_MAXH_LIST in csrc/maxh.cuh."""
+    with open(os.path.join(CSRC, "maxh.cuh")) as fh:
+        txt = fh.read()
+    line = re.search(r"#define LDPC_MAXH_LIST\(X\)(.*)", txt)
+    if not line:
+        raise RuntimeError("csrc/maxh.cuh: LDPC_MAXH_LIST not found")
+    return [int(x) for x in re.findall(r"X\((\d+)\)", line.group(1))]
+
+
+def _generated():
+    """Write (only when changed) and list the per-width translation units."""
+    os.makedirs(GEN_DIR, exist_ok=True)
+    out = []
+    for m in unroll_widths():
+        path = os.path.join(GEN_DIR, f"maxh_{m}.cu")
+        body = _GEN_TEMPLATE.format(m=m)
+        if not os.path.exists(path) or open(path).read() != body:
+            with open(path, "w") as fh:
+                fh.write(body)
+        out.append(path)
+    return out
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+            + [os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:
@@ -62,7 +103,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    srcs = _sources()
+    srcs = _generated() + _sources()  # the big instantiation units first
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB_PATH + f".tmp{os.getpid()}"

@@ -1,206 +1,26 @@
-// Layered int8 decoding of a batch of frames (sections 2 and 3).
-//
-// Work decomposition
-//   * A CTA owns a group of 4*W frames for the whole decode.  Frame 4w + l of
-//     the group sits in byte lane l of word w, so one 32-bit operation
-//     advances four frames.
-//   * E (the soft values, n bytes per frame) stays in shared memory for the
-//     whole decode: E_s[j*W + w].
-//   * L (check-to-variable messages, one byte per edge and frame) lives in a
-//     global scratch arena, edge-major with frames innermost:
-//     msg[group][(block b)*Z + row][w].  Consecutive threads handle
-//     consecutive rows, so every access of a warp is one contiguous run.
-//   * One block row is one layer.  The Z rows of a layer touch distinct
-//     variable nodes, so threads update them in parallel; layers are
-//     separated by a CTA barrier.
-//   * Per check row, the thread folds tau (Algorithm 1) forward and backward
-//     over the row's edges in ascending variable order, in registers.
-//   * After each iteration all parity checks are tested with the latest E
-//     (section 2); lanes whose syndrome matches are frozen and leave the
-//     group's stopping test; the CTA stops when every lane has stopped.
+// Host side of the batch decoder: argument checks, group width, message
+// scratch, dispatch to the kernel of the code's unroll width, and the C ABI.
+// The kernel and its launch are in decode_int8.cuh.
 #include <mutex>
+#include <string>
 
-#include "row_update.cuh"
+#include "decode_int8.cuh"
 
 namespace {
 
-using namespace lanes;
-using ldpc_dev::RowCtx;
+using ldpc_dec::DecodeArgs;
+using ldpc_dec::smem_bytes;
 
-struct DecodeArgs {
-    const int32_t* tab;
-    int Mb, nblk, Z, n, m;
-    const int8_t* llr;
-    const uint8_t* syn;
-    int batch, max_iter;
-    const uint8_t* scale_q4;
-    const int8_t* offset_q;
-    uint8_t* out_bits;
-    int32_t* out_iters;
-    uint8_t* out_ok;
-    uint32_t* msg;
-};
-
-// Threads: tid = ((row slot) * P + half) * W + w.  The two halves of a row sit
-// W lanes apart in one warp.
-template <int MAXH, int P, int W, bool TABLES, int MAXT>
-__global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int n = A.n, m = A.m, Z = A.Z, Mb = A.Mb, nblk = A.nblk;
-    const int tab_words = (int)ldpc_dev::tables_words(Mb, nblk);
-    uint32_t* E_s = reinterpret_cast<uint32_t*>(smem);
-    int32_t* s_tab = reinterpret_cast<int32_t*>(smem + (size_t)4 * n * W);
-    uint8_t* syn_s = reinterpret_cast<uint8_t*>(s_tab + tab_words);
-    __shared__ uint32_t s_bad[W], s_active[W];
-    __shared__ int s_iters[4 * W];
-
-    const int tid = threadIdx.x, T = blockDim.x;
-    const int w = tid % W, q = tid / W;
-    const int half = (P == 2) ? (q & 1) : 0;
-    const int rt = q / P, RT = T / (W * P), QT = T / W;
-    const int64_t f0 = (int64_t)blockIdx.x * 4 * W;
-    const int mbytes = (m + 7) / 8;
-
-    const ldpc_dev::Tables TB = ldpc_dev::load_tables(s_tab, A.tab, Mb, nblk, Z, W, tid, T);
-    for (int idx = tid; idx < n * W; idx += T) {
-        const int j = idx / W, ww = idx % W;
-        uint32_t word = 0;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const int64_t f = f0 + 4 * ww + l;
-            if (f < A.batch) word |= (uint32_t)(uint8_t)A.llr[f * n + j] << (8 * l);
-        }
-        E_s[idx] = word ^ kHigh;  // offset binary
+int launch(const ldpc_code* c, const DecodeArgs& A, int groups, int W, bool tables, cudaStream_t st) {
+    switch (ldpc_dec::pick_maxh(c->max_deg)) {
+#define LDPC_DECODE_CASE(M) \
+    case M:                 \
+        return ldpc_dec::decode_launch<M>(c, A, groups, W, tables, st);
+        LDPC_MAXH_LIST(LDPC_DECODE_CASE)
+#undef LDPC_DECODE_CASE
+        default:
+            return ldpc::fail(LDPC_EUNSUPPORTED, "decode: row degree above 64");
     }
-    for (int idx = tid; idx < m * W; idx += T) {
-        const int c = idx / W, ww = idx % W;
-        uint32_t nib = 0;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const int64_t f = f0 + 4 * ww + l;
-            if (f < A.batch) nib |= ((A.syn[f * mbytes + (c >> 3)] >> (c & 7)) & 1u) << l;
-        }
-        syn_s[idx] = (uint8_t)nib;
-    }
-    if (tid < W) {
-        uint32_t act = 0;
-        for (int l = 0; l < 4; ++l)
-            if (f0 + 4 * tid + l < A.batch) act |= 0xFFu << (8 * l);
-        s_active[tid] = act;
-        s_bad[tid] = 0;
-    }
-    if (tid < 4 * W) s_iters[tid] = 0;
-    __syncthreads();
-
-    const int* deg = TB.deg;
-    const int* off = TB.off;
-
-    RowCtx C;
-    C.E_s = E_s;
-    C.msg = A.msg + (size_t)blockIdx.x * nblk * Z * W;
-    C.Z = Z;
-    C.w = w;
-    C.sq = 16;
-    C.oq = 0;
-
-    for (int t = 1; t <= A.max_iter; ++t) {
-        C.active = s_active[w];
-        C.fresh = (t == 1) ? 0xFFFFFFFFu : 0u;  // messages start at 0 (stale scratch is never read)
-        for (int i = 0; i < Mb; ++i) {          // one block row = one layer, in order
-            C.d = deg[i];
-            C.b0 = off[i];
-            C.et = TB.et + C.b0;
-            if (TABLES) {
-                if (A.scale_q4) C.sq = A.scale_q4[(size_t)(t - 1) * Mb + i];
-                if (A.offset_q) C.oq = A.offset_q[(size_t)(t - 1) * Mb + i];
-            }
-            if (C.d > 0) {
-                for (int r0 = 0; r0 < Z; r0 += RT) {
-                    const int r = r0 + rt;
-                    const bool valid = r < Z;
-                    const uint32_t nib = valid ? syn_s[(i * Z + r) * W + w] : 0u;
-                    ldpc_dev::row_update_any<W, TABLES, MAXH>(C, valid ? r : 0, valid, half, nib);
-                }
-            }
-            __syncthreads();
-        }
-        // stopping test: every parity check with the latest E (section 2)
-        uint32_t bad = 0;
-        for (int c = q; c < m; c += QT) {
-            const int i = c / Z, r = c - i * Z;
-            bad |= ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
-        }
-#pragma unroll
-        for (int o = 16; o >= W; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-        if ((tid & 31) < W && bad) atomicOr(&s_bad[w], bad);
-        __syncthreads();
-        if (tid < W) {
-            const uint32_t failing = spread(s_bad[tid]);
-            const uint32_t act = s_active[tid];
-            const uint32_t newly = act & ~failing;
-            for (int l = 0; l < 4; ++l)
-                if ((newly >> (8 * l)) & 0xFFu) s_iters[4 * tid + l] = t;
-            s_active[tid] = act & failing;
-            s_bad[tid] = 0;
-        }
-        __syncthreads();
-        uint32_t live = 0;
-#pragma unroll
-        for (int ww = 0; ww < W; ++ww) live |= s_active[ww];
-        if (!live) break;
-    }
-
-    if (tid < 4 * W) {
-        const int64_t f = f0 + tid;
-        if (f < A.batch) {
-            const int it = s_iters[tid];
-            A.out_iters[f] = it ? it : A.max_iter;
-            A.out_ok[f] = it ? 1 : 0;
-        }
-    }
-    const int nb = (n + 7) / 8;
-    for (int idx = tid; idx < 4 * W * nb; idx += T) {
-        const int lane = idx / nb, b = idx - lane * nb;
-        const int64_t f = f0 + lane;
-        if (f >= A.batch) continue;
-        const int ww = lane >> 2, sbit = 8 * (lane & 3) + 7;
-        uint32_t byte = 0;
-        for (int qq = 0; qq < 8; ++qq) {
-            const int j = 8 * b + qq;
-            if (j < n) byte |= ((~E_s[j * W + ww] >> sbit) & 1u) << qq;  // E < 0 <=> stored bit 7 clear
-        }
-        A.out_bits[f * nb + b] = (uint8_t)byte;
-    }
-}
-
-size_t smem_bytes(const ldpc_code* c, int W) {
-    const size_t tab_words = (size_t)((2 * c->Mb + 1 + 1) & ~1) + 2 * (size_t)c->nblk;
-    size_t b = (size_t)4 * c->n * W + sizeof(int32_t) * tab_words + (size_t)c->m * W;
-    return (b + 15) & ~(size_t)15;
-}
-
-template <int MAXH, int W, bool TABLES>
-int launch_t(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t st) {
-    constexpr int P = 2;
-    constexpr int MAXT = MAXH <= 16 ? 1024 : 512;
-    int T = c->Z * W * P;
-    if (T > MAXT) T = MAXT;
-    T = (T + 31) / 32 * 32;
-    const size_t smem = smem_bytes(c, W);
-    auto kern = decode_kernel<MAXH, P, W, TABLES, MAXT>;
-    LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<groups, T, smem, st>>>(A);
-    ldpc::count_launch();
-    LDPC_CUDA_TRY(cudaGetLastError());
-    return LDPC_OK;
-}
-
-// Half-row length: two threads share a row, each walking ceil(d/2) edges at most.
-template <int W, bool TABLES>
-int launch_w(const ldpc_code* c, const DecodeArgs& A, int groups, cudaStream_t st) {
-    if (c->max_deg <= 24) return launch_t<12, W, TABLES>(c, A, groups, st);
-    if (c->max_deg <= 32) return launch_t<16, W, TABLES>(c, A, groups, st);
-    return launch_t<32, W, TABLES>(c, A, groups, st);
 }
 
 int pick_words(const ldpc_code* c, int batch, int smem_limit, int sms) {
@@ -235,11 +55,7 @@ int decode_common(const ldpc_code* c, const int8_t* llr, const uint8_t* syn, int
     if (rc) return rc;
     DecodeArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, llr, syn, batch, max_iter, sq, oq, bits, iters, ok,
                  reinterpret_cast<uint32_t*>(c->arena)};
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool tables = sq || oq;
-    if (W == 1) return tables ? launch_w<1, true>(c, A, (int)groups, st) : launch_w<1, false>(c, A, (int)groups, st);
-    if (W == 2) return tables ? launch_w<2, true>(c, A, (int)groups, st) : launch_w<2, false>(c, A, (int)groups, st);
-    return tables ? launch_w<4, true>(c, A, (int)groups, st) : launch_w<4, false>(c, A, (int)groups, st);
+    return launch(c, A, (int)groups, W, sq || oq, (cudaStream_t)stream);
 }
 
 }  // namespace
@@ -345,10 +161,7 @@ int ldpc_decode_batch_noalloc(const ldpc_code* code, const int8_t* llr_in, const
     if (rc) return rc;
     DecodeArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, llr_in, target_syndrome, batch, max_iter, nullptr,
                  nullptr, out_bits, out_iters, out_ok, msg};
-    cudaStream_t st = (cudaStream_t)stream;
-    if (W == 1) return launch_w<1, false>(c, A, (int)groups, st);
-    if (W == 2) return launch_w<2, false>(c, A, (int)groups, st);
-    return launch_w<4, false>(c, A, (int)groups, st);
+    return launch(c, A, (int)groups, W, false, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,301 @@
+// Persistent mixed-rate reconciliation: channel-LLR quantisation (section
+// 3.1, with the punctured/shortened positions of section 4.1) fused into the
+// layered int8 decoder (sections 2 and 3), with per-lane refill.
+//
+//   * A grid of resident CTAs pulls frames from a device work counter.  Each
+//     CTA has 4*W byte lanes; every lane decodes one frame at a time with its
+//     own iteration count.
+//   * When a lane's frame stops (first syndrome match, or its iteration cap)
+//     the CTA writes that frame's bits/iterations/flag, claims the next
+//     frame for the lane and builds its soft values straight from Bob's
+//     packed key bits, the frame's QBER and its rate counts.  Messages of a
+//     refilled lane are treated as 0 during its first iteration, so the
+//     message scratch is never cleared.
+//   * Frames of any rate, QBER and iteration count mix freely in one launch:
+//     puncturing and shortening only change the initial soft values of the
+//     shared mother code.  Per-frame results equal those of
+//     ldpc_decode_batch on the same soft values.
+#pragma once
+
+#include <math.h>
+
+#include "decode_int8.cuh"
+
+namespace ldpc_dec {
+
+struct PersistArgs {
+    const int32_t* tab;
+    int Mb, nblk, Z, n, m;
+    const uint8_t* bob;
+    const double* qber;
+    const int32_t* rank;
+    const int32_t* n_short;
+    const int32_t* n_punct;
+    const uint8_t* known;
+    const uint8_t* syn;
+    const int32_t* list;
+    int batch, list_len, max_iter;
+    double scale;
+    uint8_t* out_bits;
+    int32_t* out_iters;
+    uint8_t* out_ok;
+    uint32_t* msg;
+    int* queue;
+};
+
+// Frame id of work-list slot `slot`, or -1 past the end of the list or for an
+// id outside [0, batch).
+__device__ __forceinline__ int frame_of(const PersistArgs& A, int slot) {
+    if (slot >= A.list_len) return -1;
+    const int f = A.list ? A.list[slot] : slot;
+    return (f >= 0 && f < A.batch) ? f : -1;
+}
+
+template <int MAXH, int P, int W, int MAXT>
+__global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int n = A.n, m = A.m, Z = A.Z, Mb = A.Mb, nblk = A.nblk;
+    const int nb = (n + 7) / 8, mbytes = (m + 7) / 8;
+    const int tab_words = (int)ldpc_dev::tables_words(Mb, nblk);
+    uint32_t* E_s = reinterpret_cast<uint32_t*>(smem);
+    uint8_t* E_b = smem;
+    int32_t* s_tab = reinterpret_cast<int32_t*>(smem + (size_t)4 * n * W);
+    uint8_t* syn_s = reinterpret_cast<uint8_t*>(s_tab + tab_words);
+    constexpr int NL = 4 * W;
+    __shared__ int s_frame[NL], s_it[NL], s_mag[NL], s_ns[NL], s_np[NL];
+    __shared__ uint8_t s_done[NL], s_okf[NL];
+    __shared__ uint32_t s_active[W], s_fresh[W], s_bad[W], s_load[W];
+    __shared__ int s_base, s_any_load, s_any_done;
+
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int w = tid % W, q = tid / W;
+    const int half = (P == 2) ? (q & 1) : 0;
+    const int rt = q / P, RT = T / (W * P), QT = T / W;
+
+    const ldpc_dev::Tables TB = ldpc_dev::load_tables(s_tab, A.tab, Mb, nblk, Z, W, tid, T);
+    if (tid == 0) s_base = atomicAdd(A.queue, NL);
+    if (tid < W) {
+        s_active[tid] = 0;
+        s_fresh[tid] = 0;
+        s_bad[tid] = 0;
+        s_load[tid] = 0;
+    }
+    __syncthreads();
+    if (tid < NL) {
+        const int slot = s_base + tid;
+        s_frame[tid] = frame_of(A, slot);
+        s_done[tid] = 0;
+    }
+    __syncthreads();
+    if (tid < W) {
+        uint32_t ld = 0;
+        for (int l = 0; l < 4; ++l)
+            if (s_frame[4 * tid + l] >= 0) ld |= 0xFFu << (8 * l);
+        s_load[tid] = ld;
+    }
+    if (tid == 0) s_any_load = 1;
+
+    const int* deg = TB.deg;
+    const int* off = TB.off;
+    RowCtx C;
+    C.E_s = E_s;
+    C.msg = A.msg + (size_t)blockIdx.x * nblk * Z * W;
+    C.Z = Z;
+    C.w = w;
+    C.sq = 16;
+    C.oq = 0;
+
+    for (;;) {
+        __syncthreads();
+        // ---- refill: soft values and syndrome bits of newly claimed frames
+        if (s_any_load) {
+            if (tid < NL) {
+                const int ww = tid >> 2, l = tid & 3;
+                if ((s_load[ww] >> (8 * l)) & 1u) {
+                    const int f = s_frame[tid];
+                    const double qb = A.qber[f];
+                    long mag = lround(log((1.0 - qb) / qb) * A.scale);
+                    s_mag[tid] = (int)(mag > 127 ? 127 : (mag < -127 ? -127 : mag));
+                    s_ns[tid] = A.n_short ? A.n_short[f] : 0;
+                    s_np[tid] = A.n_punct ? A.n_punct[f] : 0;
+                    s_it[tid] = 0;
+                }
+            }
+            __syncthreads();
+            for (int j = tid; j < n; j += T) {
+                const int rk = A.rank ? A.rank[j] : 0x7FFFFFFF;
+                for (int lane = 0; lane < NL; ++lane) {
+                    const int ww = lane >> 2, l = lane & 3;
+                    if (!((s_load[ww] >> (8 * l)) & 1u)) continue;
+                    const int64_t f = s_frame[lane];
+                    const int y = (A.bob[f * nb + (j >> 3)] >> (j & 7)) & 1;
+                    int x = y ? -s_mag[lane] : s_mag[lane];
+                    if (rk < s_ns[lane]) x = ((A.known[f * nb + (j >> 3)] >> (j & 7)) & 1) ? -127 : 127;
+                    else if (rk < s_ns[lane] + s_np[lane]) x = 0;
+                    E_b[((size_t)j * W + ww) * 4 + l] = (uint8_t)((int8_t)x) ^ 0x80u;
+                }
+            }
+            for (int c = tid; c < m; c += T) {
+                for (int ww = 0; ww < W; ++ww) {
+                    const uint32_t ld = s_load[ww];
+                    if (!ld) continue;
+                    uint32_t nib = syn_s[c * W + ww] & 0xFu;  // lanes not being loaded keep their bits
+                    for (int l = 0; l < 4; ++l) {
+                        if (!((ld >> (8 * l)) & 1u)) continue;
+                        const int64_t f = s_frame[4 * ww + l];
+                        const uint32_t bit = (A.syn[f * mbytes + (c >> 3)] >> (c & 7)) & 1u;
+                        nib = (nib & ~(1u << l)) | (bit << l);
+                    }
+                    syn_s[c * W + ww] = (uint8_t)nib;
+                }
+            }
+            __syncthreads();
+            if (tid < W) {
+                s_active[tid] |= s_load[tid];
+                s_fresh[tid] |= s_load[tid];
+                s_load[tid] = 0;
+            }
+            if (tid == 0) s_any_load = 0;
+            __syncthreads();
+        }
+        uint32_t live = 0;
+#pragma unroll
+        for (int ww = 0; ww < W; ++ww) live |= s_active[ww];
+        if (!live) break;
+
+        // ---- one iteration of every active lane
+        C.active = s_active[w];
+        C.fresh = s_fresh[w];
+        for (int i = 0; i < Mb; ++i) {
+            C.d = deg[i];
+            C.b0 = off[i];
+            C.et = TB.et + C.b0;
+            if (C.d > 0) {
+                for (int r0 = 0; r0 < Z; r0 += RT) {
+                    const int r = r0 + rt;
+                    const bool valid = r < Z;
+                    const uint32_t nib = valid ? syn_s[(i * Z + r) * W + w] : 0u;
+                    ldpc_dev::row_update_any<W, false, MAXH>(C, valid ? r : 0, valid, half, nib);
+                }
+            }
+            __syncthreads();
+        }
+        uint32_t bad = 0;
+        for (int c = q; c < m; c += QT) {
+            const int i = c / Z, r = c - i * Z;
+            bad |= ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
+        }
+#pragma unroll
+        for (int o = 16; o >= W; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        if ((tid & 31) < W && bad) atomicOr(&s_bad[w], bad);
+        if (tid == 0) s_any_done = 0;
+        __syncthreads();
+
+        // ---- per-lane bookkeeping (one thread per word)
+        if (tid < W) {
+            const uint32_t failing = spread(s_bad[tid]);
+            uint32_t act = s_active[tid];
+            for (int l = 0; l < 4; ++l) {
+                const uint32_t lm = 0xFFu << (8 * l);
+                if (!(act & lm)) continue;
+                const int lane = 4 * tid + l;
+                const int it = ++s_it[lane];
+                const bool ok = !(failing & lm);
+                if (ok || it >= A.max_iter) {
+                    s_done[lane] = 1;
+                    s_okf[lane] = ok ? 1 : 0;
+                    act &= ~lm;
+                    s_any_done = 1;
+                }
+            }
+            s_active[tid] = act;
+            s_fresh[tid] = 0;
+            s_bad[tid] = 0;
+        }
+        __syncthreads();
+        if (!s_any_done) continue;
+
+        // ---- results of finished frames (E of a finished lane is frozen)
+        for (int idx = tid; idx < NL * nb; idx += T) {
+            const int lane = idx / nb, b = idx - lane * nb;
+            if (!s_done[lane]) continue;
+            const int64_t f = s_frame[lane];
+            const int ww = lane >> 2, sbit = 8 * (lane & 3) + 7;
+            uint32_t byte = 0;
+            for (int qq = 0; qq < 8; ++qq) {
+                const int j = 8 * b + qq;
+                if (j < n) byte |= ((~E_s[j * W + ww] >> sbit) & 1u) << qq;
+            }
+            A.out_bits[f * nb + b] = (uint8_t)byte;
+        }
+        if (tid < NL && s_done[tid]) {
+            const int64_t f = s_frame[tid];
+            A.out_iters[f] = s_it[tid];
+            A.out_ok[f] = s_okf[tid];
+        }
+        __syncthreads();
+        // ---- claim the next frames for the finished lanes
+        if (tid == 0) {
+            int k = 0;
+            for (int lane = 0; lane < NL; ++lane) k += s_done[lane];
+            const int base = atomicAdd(A.queue, k);
+            int i = 0;
+            for (int lane = 0; lane < NL; ++lane) {
+                if (!s_done[lane]) continue;
+                s_done[lane] = 0;
+                s_frame[lane] = frame_of(A, base + i++);
+                if (s_frame[lane] >= 0) {
+                    s_load[lane >> 2] |= 0xFFu << (8 * (lane & 3));
+                    s_any_load = 1;
+                }
+            }
+        }
+    }
+}
+
+
+template <int MAXH, int W>
+int launch_p(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int* grid_out, bool dry, cudaStream_t st) {
+    constexpr int P = 2;
+    constexpr int MAXT = max_threads<MAXH>();
+    int T = c->Z * W * P;
+    if (T > MAXT) T = MAXT;
+    T = (T + 31) / 32 * 32;
+    const size_t smem = smem_bytes(c, W);
+    auto kern = persistent_kernel<MAXH, P, W, MAXT>;
+    LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0, sms = 0;
+    LDPC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem));
+    LDPC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (occ < 1) return ldpc::fail(LDPC_EUNSUPPORTED, "persistent decode: kernel does not fit on an SM");
+    int per_sm = ctas_per_sm > 0 ? (ctas_per_sm < occ ? ctas_per_sm : occ) : occ;
+    int64_t grid = (int64_t)sms * per_sm;
+    const int64_t need = ((int64_t)A.list_len + 4 * W - 1) / (4 * W);
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    *grid_out = (int)grid;
+    if (dry) return LDPC_OK;
+    LDPC_CUDA_TRY(cudaMemsetAsync(A.queue, 0, sizeof(int), st));
+    kern<<<(int)grid, T, smem, st>>>(A);
+    ldpc::count_launch();
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+// Launch (or with dry, only size the grid of) the persistent decoder of
+// width MAXH with W words per row.  Instantiated once per width, each in its
+// own translation unit.
+template <int MAXH>
+int persist_launch(const ldpc_code* c, const PersistArgs& A, int W, int ctas_per_sm, int* grid, bool dry,
+                   cudaStream_t st) {
+    if (W == 1) return launch_p<MAXH, 1>(c, A, ctas_per_sm, grid, dry, st);
+    if (W == 2) return launch_p<MAXH, 2>(c, A, ctas_per_sm, grid, dry, st);
+    return launch_p<MAXH, 4>(c, A, ctas_per_sm, grid, dry, st);
+}
+
+#define LDPC_PERSIST_EXTERN(M) \
+    extern template int persist_launch<M>(const ldpc_code*, const PersistArgs&, int, int, int*, bool, cudaStream_t);
+LDPC_MAXH_LIST(LDPC_PERSIST_EXTERN)
+#undef LDPC_PERSIST_EXTERN
+
+}  // namespace ldpc_dec

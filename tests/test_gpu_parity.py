@@ -223,3 +223,28 @@ def test_decode_is_deterministic_and_batch_independent():
     one = [t.cpu().numpy() for t in code.decode(L[13:14].contiguous(), S[13:14].contiguous(), 30)]
     for a, b in zip(r1, one):
         assert np.array_equal(a[13], b[0])
+
+
+@pytest.mark.parametrize("dmax", [3, 8, 12, 17, 19, 21, 23, 25, 27, 31, 45, 60])
+def test_every_unroll_width_batch_and_persistent(dmax):
+    """Codes whose longest row lands on each compiled unroll width (and on
+    the row sizes just below a width); rows of several degrees per code so
+    that slots past a layer's degree are exercised too."""
+    from paper_1903_10107_gb300.decoder import QCCode
+    Z, Nb = 16, max(dmax, 6)
+    g = np.random.default_rng(dmax)
+    degs = [dmax, max(1, dmax // 2), max(1, (2 * dmax) // 3), 1 + dmax % 3]
+    base = np.full((len(degs), Nb), -1, dtype=np.int32)
+    for i, d in enumerate(degs):
+        cols = g.choice(Nb, size=d, replace=False)
+        base[i, cols] = g.integers(0, Z, size=d)
+    B, q, T = 13, 0.04, 12
+    xa, yb = _frames(base, Z, B, q, 100 + dmax)
+    llr, syn_u = _oracle_inputs(base, Z, xa, yb, q)
+    gg, o = _decode_both(base, Z, llr, syn_u, T)
+    _assert_same(gg, o)
+    code = QCCode(base, Z)
+    qv = np.full(B, q)
+    bits, iters, ok = code.reconcile_persistent(_cuda(yb), _cuda(qv), _cuda(inputs.pack_bits(syn_u)), T)
+    torch.cuda.synchronize()
+    _assert_same((inputs.unpack_bits(bits.cpu().numpy(), code.n), iters.cpu().numpy(), ok.cpu().numpy()), o)
