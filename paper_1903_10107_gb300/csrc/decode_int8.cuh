@@ -127,9 +127,18 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
         }
         // stopping test: every parity check with the latest E (section 2)
         uint32_t bad = 0;
-        for (int c = q; c < m; c += QT) {
-            const int i = c / Z, r = c - i * Z;
-            bad |= ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
+        {
+            int i = q / Z, r = q - i * Z;
+            const int di = QT / Z, dr = QT - di * Z;
+            for (int c = q; c < m; c += QT) {
+                bad |= ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
+                r += dr;
+                i += di;
+                if (r >= Z) {
+                    r -= Z;
+                    ++i;
+                }
+            }
         }
 #pragma unroll
         for (int o = 16; o >= W; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);

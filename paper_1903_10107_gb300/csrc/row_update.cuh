@@ -105,21 +105,18 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
             idx[j] = t.x + wrap(r + t.y, Z) * W + C.w;
         }
     }
+    // One pass per slot: |E - L| and its sign, then the left fold.  (A
+    // separate pass for each doubles the guard branches of the unrolled slots.)
+    uint32_t tot = kMax;
 #pragma unroll(HMAX)
     for (int j = 0; j < HMAX; ++j) {
         if (j < cnt) {
             const uint32_t e = C.E_s[idx[j]];
             const uint32_t lb = select(C.fresh, kHigh, av[j]);  // stale lanes read as 0
             const uint32_t sv = lt_u8(e, lb);    // sign of E - L
-            av[j] = cap127(absdiff(e, lb)) | sv; // |sat8(E - L)| and its sign
+            const uint32_t a = cap127(absdiff(e, lb));  // |sat8(E - L)|
+            av[j] = a | sv;
             S ^= sv;
-        }
-    }
-    uint32_t tot = kMax;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < cnt) {
-            const uint32_t a = av[j] & kMax;
             tot = (j == 0) ? a : tau(tot, a);
             F[j] = tot;
         }
@@ -174,7 +171,12 @@ template <int W>
 __device__ __forceinline__ uint32_t row_parity(const uint32_t* E_s, const int2* et, int d, int r, int Z, int w,
                                                uint32_t syn_nib) {
     uint32_t p = nibble_to_high(syn_nib) ^ ((d & 1) ? kHigh : 0u);
-    for (int k = 0; k < d; ++k) {
+    int k = 0;
+    for (; k + 2 <= d; k += 2) {
+        const int2 t0 = et[k], t1 = et[k + 1];
+        p ^= E_s[t0.x + wrap(r + t0.y, Z) * W + w] ^ E_s[t1.x + wrap(r + t1.y, Z) * W + w];
+    }
+    if (k < d) {
         const int2 t = et[k];
         p ^= E_s[t.x + wrap(r + t.y, Z) * W + w];
     }
