@@ -146,11 +146,16 @@ def peaks():
 
 
 def kernel_sources_sha():
+    """Hash of the decoder kernels' code, comments and whitespace removed (a
+    profile taken before a comment-only edit still describes the kernel)."""
     h = hashlib.sha256()
     for fn in ("decode_int8.cu", "decode_int8.cuh", "decode_persistent.cu", "decode_persistent.cuh", "maxh.cuh",
                "row_update.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_1903_10107_gb300", "csrc", fn), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1903_10107_gb300", "csrc", fn)) as fh:
+            txt = fh.read()
+        txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", " ", txt)
+        h.update(" ".join(txt.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -13,8 +13,9 @@
 //   * One block row is one layer.  The Z rows of a layer touch distinct
 //     variable nodes, so threads update them in parallel; layers are
 //     separated by a CTA barrier.
-//   * Per check row, the thread folds tau (Algorithm 1) forward and backward
-//     over the row's edges in ascending variable order, in registers.
+//   * Two threads share a check row: they fold tau (Algorithm 1) forward and
+//     backward over the row's edges in ascending variable order, in
+//     registers (row_update.cuh), unrolled for the code's width (maxh.cuh).
 //   * After each iteration all parity checks are tested with the latest E
 //     (section 2); lanes whose syndrome matches are frozen and leave the
 //     group's stopping test; the CTA stops when every lane has stopped.
