@@ -27,11 +27,17 @@ namespace {
 
 constexpr float kEmpty = 50.0f;  // empty box-plus of a degree-1 row
 
+// beta_k(x, y) = min(x, y) + k * ln((1 + e^{-(x+y)/k}) / (1 + e^{-|x-y|/k})) for
+// x, y >= 0: the ratio lies in [1/2, 1], so the single logarithm of it has a
+// small absolute error, and the hardware exponential, logarithm and division
+// (__expf, __logf, __fdividef) replace the two log1p/exp library sequences.
+// The result is symmetric in x and y bit for bit.
 __device__ __forceinline__ float bplus(float x, float y, float kap, float ikap) {
-    return fminf(x, y) + kap * (log1pf(expf(-(x + y) * ikap)) - log1pf(expf(-fabsf(x - y) * ikap)));
+    const float a = __expf(-(x + y) * ikap), b = __expf(-fabsf(x - y) * ikap);
+    return fminf(x, y) + kap * __logf(__fdividef(1.0f + a, 1.0f + b));
 }
 
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
+__device__ __forceinline__ float sigm(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
@@ -272,7 +278,7 @@ __host__ __device__ inline Shape cta_shape(int Z) {
 }
 
 template <int HMAX>
-__global__ void __launch_bounds__(512) relaxed_forward_kernel(RelaxArgs A) {
+__global__ void __launch_bounds__(512, 2) relaxed_forward_kernel(RelaxArgs A) {
     extern __shared__ __align__(16) float fsm[];
     const int Z = A.Z, n = A.n;
     const Shape sh = cta_shape(Z);
