@@ -158,23 +158,19 @@ __device__ __forceinline__ void row_backward(float* G, const float* Vrow, float*
                                              int dtrue, int half, int r, int Z, float S, float al, float ga,
                                              float kap, float ikap, float& acc_a, float& acc_g) {
     const RowHalf H = row_half(d, half);
-    float a[HMAX], O[HMAX], X[HMAX], gO[HMAX], gX[HMAX], gA[HMAX];
-    int idx[HMAX];
+    float a[HMAX], O[HMAX], X[HMAX], gO[HMAX], gA[HMAX];
     uint32_t neg = 0;  // bit j: v_j < 0
     float sgn = 1.0f;
 #pragma unroll(HMAX)
     for (int j = 0; j < HMAX; ++j) {
         if (j < H.cnt) {
-            const int k = H.k0 + j * H.kdir;
-            const int2 t = et[k];
-            idx[j] = t.x + ldpc_dev::wrap(r + t.y, Z);
-            const float v = Vrow[(size_t)k * Z];
+            const float v = Vrow[(size_t)(H.k0 + j * H.kdir) * Z];
             a[j] = fabsf(v);
             if (v < 0.0f) {
                 neg |= 1u << j;
                 sgn = -sgn;
             }
-            gO[j] = gX[j] = gA[j] = 0.0f;
+            gO[j] = gA[j] = 0.0f;
         }
     }
     float tot = kEmpty;
@@ -195,70 +191,60 @@ __device__ __forceinline__ void row_backward(float* G, const float* Vrow, float*
             if (j > 0) x = bplus(a[j], x, kap, ikap);
         }
     }
-    // magnitudes, their adjoints, and the adjoint through m_j = beta(O_{j-1}, X_j)
+    // Ascending: the magnitude m_j = beta(O_{j-1}, X_j) of every slot and its
+    // adjoint, and with it the adjoint of the partner chain X_{j-1} =
+    // beta(a_j, X_j), carried as one running value g (the adjoint of X_j);
+    // what reaches the far end belongs to the partner's fold total.
+    float g = 0.0f;
 #pragma unroll(HMAX)
     for (int j = 0; j < HMAX; ++j) {
         if (j < H.cnt) {
             const int k = H.k0 + j * H.kdir;
+            const int2 t = et[k];
             const float B = (j == 0) ? X[0] : bplus(O[j >= 1 ? j - 1 : 0], X[j], kap, ikap);
             const float sj = ((neg >> j) & 1u) ? -S : S;
-            const float gtot = gLrow[(size_t)k * Z] + G[idx[j]];  // L_new feeds E (Eq. 9) and the next iteration
+            const float gtot = gLrow[(size_t)k * Z] + G[t.x + ldpc_dev::wrap(r + t.y, Z)];  // L_new feeds E and the next iteration
             const float gmag = gtot * sj;
             const bool pos = B > ga;
             acc_a += gmag * fmaxf(B - ga, 0.0f);
             acc_g -= pos ? gmag * al : 0.0f;
             const float gm = (pos && dtrue > 1) ? gmag * al : 0.0f;
             if (j == 0) {
-                gX[0] += gm;
+                g = gm;
             } else {
-                float dx, dy;
+                float dx, dy, cx, cy;
                 bplus_grad(O[j >= 1 ? j - 1 : 0], X[j], ikap, dx, dy);
                 gO[j >= 1 ? j - 1 : 0] += gm * dx;
-                gX[j] += gm * dy;
+                bplus_grad(a[j], X[j], ikap, cx, cy);
+                gA[j] += g * cx;
+                g = gm * dy + g * cy;
             }
         }
     }
-    // partner chain X_{j-1} = beta(a_j, X_j), ascending: the adjoint that
-    // reaches the far end belongs to the partner's fold total
-    float g = 0.0f;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < H.cnt) {
-            if (j == 0) {
-                g = gX[0];
-            } else {
-                float dx, dy;
-                bplus_grad(a[j], X[j], ikap, dx, dy);
-                gA[j] += g * dx;
-                g = gX[j] + g * dy;
-            }
-        }
-    }
-    // own fold O_j = beta(O_{j-1}, a_j), descending, starting from the
-    // adjoint of the total that the partner's chain sends back
+    // Descending: the own fold O_j = beta(O_{j-1}, a_j), starting from the
+    // adjoint of the total that the partner's chain sends back; each slot's
+    // adjoint is complete once its step is done, so it is written out there.
     float go = __shfl_xor_sync(0xffffffffu, g, 1);
 #pragma unroll(HMAX)
     for (int jj = 0; jj < HMAX; ++jj) {
         const int j = HMAX - 1 - jj;
         if (j < H.cnt) {
             go += gO[j];
+            float ga_j = gA[j];
             if (j > 0) {
                 float dx, dy;
                 bplus_grad(O[j >= 1 ? j - 1 : 0], a[j], ikap, dx, dy);
-                gA[j] += go * dy;
+                ga_j += go * dy;
                 go *= dx;
             } else {
-                gA[0] += go;
+                ga_j += go;
             }
-        }
-    }
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < H.cnt) {
             const int k = H.k0 + j * H.kdir;
-            const float gv = G[idx[j]] + gA[j] * (((neg >> j) & 1u) ? -1.0f : 1.0f);  // d|v|/dv = sign(v)
-            G[idx[j]] = gv;                                                           // adjoint of E before the layer
-            gLrow[(size_t)k * Z] = -gv;                                               // adjoint of the old message (Eq. 8)
+            const int2 t = et[k];
+            const int vi = t.x + ldpc_dev::wrap(r + t.y, Z);
+            const float gv = G[vi] + ga_j * (((neg >> j) & 1u) ? -1.0f : 1.0f);  // d|v|/dv = sign(v)
+            G[vi] = gv;                                                         // adjoint of E before the layer
+            gLrow[(size_t)k * Z] = -gv;                                         // adjoint of the old message (Eq. 8)
         }
     }
 }
@@ -344,7 +330,7 @@ __global__ void __launch_bounds__(512, 2) relaxed_forward_kernel(RelaxArgs A) {
 }
 
 template <int HMAX>
-__global__ void __launch_bounds__(512) relaxed_backward_kernel(RelaxArgs A) {
+__global__ void __launch_bounds__(512, 2) relaxed_backward_kernel(RelaxArgs A) {
     extern __shared__ __align__(16) float fsm[];
     const int Z = A.Z, n = A.n;
     const Shape sh = cta_shape(Z);
