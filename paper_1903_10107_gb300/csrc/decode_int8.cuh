@@ -105,6 +105,8 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
     C.sq = 16;
     C.oq = 0;
 
+    // the stopping test's rows of this thread: c = q + k QT, layer i, row r
+    const int pq_i0 = q / Z, pq_r0 = q - pq_i0 * Z, pq_di = QT / Z, pq_dr = QT - pq_di * Z;
     for (int t = 1; t <= A.max_iter; ++t) {
         C.active = s_active[w];
         C.fresh = (t == 1) ? 0xFFFFFFFFu : 0u;  // messages start at 0 (stale scratch is never read)
@@ -129,12 +131,14 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
         // stopping test: every parity check with the latest E (section 2)
         uint32_t bad = 0;
         {
-            int i = q / Z, r = q - i * Z;
-            const int di = QT / Z, dr = QT - di * Z;
+            int i = pq_i0, r = pq_r0;  // layer and row of check c = q + k QT
             for (int c = q; c < m; c += QT) {
-                bad |= ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
-                r += dr;
-                i += di;
+                const int d = deg[i];
+                const int2* et = TB.et + off[i];
+                const uint32_t nib = syn_s[c * W + w];
+                bad |= ldpc_dev::row_parity<W>(E_s, et, d, r, Z, w, nib);
+                r += pq_dr;
+                i += pq_di;
                 if (r >= Z) {
                     r -= Z;
                     ++i;
