@@ -203,6 +203,14 @@ class ReconciliationServer:
                         inflight += 1
                         progressed = True
             if not progressed:
+                if inflight == 0:
+                    for e in self.codes.values():
+                        if e.queue and not self._admissible(e, 1):
+                            # nothing in flight will free memory: this request can never start
+                            raise RuntimeError(
+                                f"serving: a request of code {e.name} needs {self._need(e, 1)} device bytes; "
+                                f"the budget ({self.mem_budget or 'none'}) or free memory minus the reserve "
+                                f"({self.reserve}) is smaller")
                 time.sleep(0.0002)
         torch.cuda.synchronize(self.device)
         return pending
