@@ -112,6 +112,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB_PATH)
+    try:  # launch shapes tuned for the previous kernels no longer apply
+        os.remove(os.path.join(OUT_DIR, "autotune.json"))
+    except FileNotFoundError:
+        pass
     return LIB_PATH
 
 
