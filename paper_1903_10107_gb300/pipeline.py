@@ -278,7 +278,9 @@ class InteractiveProtocol:
         for rnd in range(self.max_rounds + 1):
             d_np = torch.from_numpy(n_punct).to(dev)
             d_ns = torch.from_numpy(n_short).to(dev)
-            d_list = torch.from_numpy(todo).to(dev)
+            # the frames still to decode, most punctured / highest QBER first
+            d_list = torch.from_numpy(np.ascontiguousarray(
+                todo[hardest_first(n_punct[todo], n_short[todo], q[todo])])).to(dev)
             self.code.reconcile_persistent(bob, d_q, syn, self.max_iter, rank=self.rec.rank, n_short=d_ns,
                                            n_punct=d_np, known=known, frame_list=d_list,
                                            llr_scale=self.rec.llr_scale, words=self.words,
