@@ -188,7 +188,9 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": res["value"], "unit": "Mbps", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-        "config": {"workload": w.name, "frames_per_step": res["frames"], "n": w.n, "max_iter": w.max_iter},
+        "config": {"workload": w.name, "frames": B * world, "n": w.n, "m": w.m, "Z": w.Z, "max_iter": w.max_iter,
+                   "qber": list(w.qber) if isinstance(w.qber, tuple) else w.qber, "target_f": w.target_f,
+                   "llr_lsb_per_nat": round(w.llr_scale, 4), "sample_frames_per_step": res["frames"]},
         "cpu_baseline": {"value": res["value"], "unit": "Mbps", "cores": res["cores"], "kind": "oracle",
                          "sample": res["sample"]},
         "e2e": {"value": res["value"], "unit": "Mbps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
