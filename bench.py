@@ -159,6 +159,30 @@ def kernel_sources_sha():
     return h.hexdigest()[:16]
 
 
+# Integer work of the method per edge and frame-iteration, in byte operations:
+# Eq. 8 (difference, saturation), the sign product of Eq. 1, three box-plus
+# evaluations of Algorithm 1 in the forward-backward fold (min, |difference|,
+# five range tests, corrections: about 10 each) and Eq. 9 with Algorithm 2's
+# guard; about 40 in all.
+ALU_OPS_PER_EDGE = 40
+
+
+def roofline_alu(it_sum, edges, seconds, clk):
+    """The integer-issue roofline of the decoder: byte operations of the method
+    per second against what the SMs can issue, 152 SMs x 4 schedulers x 32
+    lanes x the SM clock seen during the run x 4 byte lanes per 32-bit
+    operation (the ALU and FMA pipes each take 16 lanes per scheduler and
+    cycle, the scheduler issues one 32-lane instruction per cycle)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * 4 * 32 * float(mhz) * 1e6 * 4 / 1e12
+    achieved = ALU_OPS_PER_EDGE * float(edges) * float(it_sum) / seconds / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T byte-op/s", "frac": achieved / peak,
+            "ops_per_edge_frame_iteration": ALU_OPS_PER_EDGE,
+            "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {float(mhz):.0f} MHz x 4 byte lanes"}
+
+
 def profiled_traffic(kernel: str, workload: str, launch_frames: int):
     """DRAM bytes per launch from the committed ncu summary of the kernel, if
     it was taken on the current kernel source; else None."""
@@ -460,6 +484,7 @@ def run_ours(args, rank, world, dist):
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": kernel_name, "kernel_ms": dec_s * 1e3,
                      "algorithmic_bytes": alg_bytes},
+        "roofline_alu": roofline_alu(it_sum, code.edges, dec_s, clk),
         "e2e": {"value": e_tot / e2e_max / 1e6, "unit": "Mbps", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
