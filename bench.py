@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (for small runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--max-iter", type=int, default=0, help="override the workload's iteration cap")
+    ap.add_argument("--target-f", type=float, default=0.0,
+                    help="override the mixed-rate workload's target efficiency (rate plan per frame)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-order", action="store_true", help="persistent launch takes frames in index order")
@@ -204,6 +206,10 @@ def run_reference(args, rank, world):
         return
     from oracle import core as orc
     w = inputs.WORKLOADS[args.workload]
+    if args.max_iter:
+        w.max_iter = args.max_iter
+    if args.target_f and w.mixed_rate:
+        w.target_f = args.target_f
     B = args.batch or w.batch
     # size a per-step sample of about (cpu_seconds / (steps + warmup)) of oracle time
     per_step = max(2.0, args.cpu_seconds * 4 / max(1, args.steps + args.warmup))
@@ -307,6 +313,8 @@ def run_ours(args, rank, world, dist):
     w = inputs.WORKLOADS[args.workload]
     if args.max_iter:
         w.max_iter = args.max_iter
+    if args.target_f and w.mixed_rate:
+        w.target_f = args.target_f
     first, B = sharding.weak_shard(args.batch or w.batch, rank, world)  # every rank its own frames
     bt = Batch(w, B, first)
     rec = Reconciler(bt.base, w.Z, bt.tiebreak, dev, llr_scale=w.llr_scale)
