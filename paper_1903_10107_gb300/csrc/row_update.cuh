@@ -155,10 +155,10 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
     }
 }
 
-// One body per kernel: MAXH bounds ceil(d/2) over all layers of the code
-// (12: degrees up to 24; 16: up to 32; 32: up to 64).  A single body keeps
-// register allocation tight; the guarded slots past a layer's degree are the
-// price of irregular codes.
+// One body per kernel: MAXH bounds ceil(d/2) over all layers of the code (the
+// smallest compiled width that holds the longest row, maxh.cuh).  A single
+// body keeps register allocation tight; the guarded slots past a layer's
+// degree are the price of irregular codes.
 template <int W, bool TABLES, int MAXH>
 __device__ __forceinline__ void row_update_any(const RowCtx& C, int r, bool valid, int half, uint32_t syn_nib) {
     row_update<MAXH, W, TABLES>(C, r, valid, half, syn_nib);
