@@ -122,31 +122,51 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
                 }
             }
             __syncthreads();
-            for (int j = tid; j < n; j += T) {
-                const int rk = A.rank ? A.rank[j] : 0x7FFFFFFF;
+            // soft values: one byte of Bob's key (8 variables) per thread and step,
+            // every load of the step issued before the stores that use them
+            for (int b = tid; b < nb; b += T) {
+                const int j0 = b << 3;
+                int rk[8];
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) rk[qq] = (A.rank && j0 + qq < n) ? A.rank[j0 + qq] : 0x7FFFFFFF;
                 for (int lane = 0; lane < NL; ++lane) {
                     const int ww = lane >> 2, l = lane & 3;
                     if (!((s_load[ww] >> (8 * l)) & 1u)) continue;
                     const int64_t f = s_frame[lane];
-                    const int y = (A.bob[f * nb + (j >> 3)] >> (j & 7)) & 1;
-                    int x = y ? -s_mag[lane] : s_mag[lane];
-                    if (rk < s_ns[lane]) x = ((A.known[f * nb + (j >> 3)] >> (j & 7)) & 1) ? -127 : 127;
-                    else if (rk < s_ns[lane] + s_np[lane]) x = 0;
-                    E_b[((size_t)j * W + ww) * 4 + l] = (uint8_t)((int8_t)x) ^ 0x80u;
+                    const int ns = s_ns[lane], np = s_np[lane], mag = s_mag[lane];
+                    const uint32_t yb = A.bob[f * nb + b];
+                    const uint32_t kb = (ns > 0) ? A.known[f * nb + b] : 0u;  // shortening implies known values
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq) {
+                        const int j = j0 + qq;
+                        if (j >= n) break;
+                        int x = ((yb >> qq) & 1u) ? -mag : mag;
+                        if (rk[qq] < ns) x = ((kb >> qq) & 1u) ? -127 : 127;
+                        else if (rk[qq] < ns + np) x = 0;
+                        E_b[((size_t)j * W + ww) * 4 + l] = (uint8_t)((int8_t)x) ^ 0x80u;
+                    }
                 }
             }
-            for (int c = tid; c < m; c += T) {
+            // syndrome bits: one byte of each claimed frame's syndrome (8 checks) per thread and step
+            for (int sb = tid; sb < mbytes; sb += T) {
+                const int c0 = sb << 3;
                 for (int ww = 0; ww < W; ++ww) {
                     const uint32_t ld = s_load[ww];
                     if (!ld) continue;
-                    uint32_t nib = syn_s[c * W + ww] & 0xFu;  // lanes not being loaded keep their bits
-                    for (int l = 0; l < 4; ++l) {
-                        if (!((ld >> (8 * l)) & 1u)) continue;
-                        const int64_t f = s_frame[4 * ww + l];
-                        const uint32_t bit = (A.syn[f * mbytes + (c >> 3)] >> (c & 7)) & 1u;
-                        nib = (nib & ~(1u << l)) | (bit << l);
+                    uint32_t sy[4];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                        sy[l] = ((ld >> (8 * l)) & 1u) ? A.syn[(int64_t)s_frame[4 * ww + l] * mbytes + sb] : 0u;
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq) {
+                        const int c = c0 + qq;
+                        if (c >= m) break;
+                        uint32_t nib = syn_s[c * W + ww] & 0xFu;  // lanes not being loaded keep their bits
+#pragma unroll
+                        for (int l = 0; l < 4; ++l)
+                            if ((ld >> (8 * l)) & 1u) nib = (nib & ~(1u << l)) | (((sy[l] >> qq) & 1u) << l);
+                        syn_s[c * W + ww] = (uint8_t)nib;
                     }
-                    syn_s[c * W + ww] = (uint8_t)nib;
                 }
             }
             __syncthreads();
@@ -225,17 +245,26 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
         if (!s_any_done) continue;
 
         // ---- results of finished frames (E of a finished lane is frozen)
-        for (int idx = tid; idx < NL * nb; idx += T) {
-            const int lane = idx / nb, b = idx - lane * nb;
-            if (!s_done[lane]) continue;
-            const int64_t f = s_frame[lane];
-            const int ww = lane >> 2, sbit = 8 * (lane & 3) + 7;
-            uint32_t byte = 0;
-            for (int qq = 0; qq < 8; ++qq) {
-                const int j = 8 * b + qq;
-                if (j < n) byte |= ((~E_s[j * W + ww] >> sbit) & 1u) << qq;
+        for (int b = tid; b < nb; b += T) {  // one byte of output (8 variables) per thread and step
+            for (int ww = 0; ww < W; ++ww) {
+                uint32_t dmask = 0;  // finished lanes of this word
+#pragma unroll
+                for (int l = 0; l < 4; ++l) dmask |= (uint32_t)s_done[4 * ww + l] << l;
+                if (!dmask) continue;
+                uint32_t e[8];
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    const int j = 8 * b + qq;
+                    e[qq] = (j < n) ? E_s[j * W + ww] : 0xFFFFFFFFu;  // past n: bit 7 set, output bit 0
+                }
+                for (int l = 0; l < 4; ++l) {
+                    if (!((dmask >> l) & 1u)) continue;
+                    uint32_t byte = 0;
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq) byte |= ((~e[qq] >> (8 * l + 7)) & 1u) << qq;  // E < 0 <=> bit 7 clear
+                    A.out_bits[(int64_t)s_frame[4 * ww + l] * nb + b] = (uint8_t)byte;
+                }
             }
-            A.out_bits[f * nb + b] = (uint8_t)byte;
         }
         if (tid < NL && s_done[tid]) {
             const int64_t f = s_frame[tid];
