@@ -43,6 +43,11 @@ struct DecodeArgs {
     uint32_t* msg;
 };
 
+// Shared memory of a CTA: soft values (4 n W bytes), the code tables from the
+// next 16-byte boundary (their int2 edge entries need 8-byte alignment, and
+// 4 n W is only a multiple of 4 when n is odd), then the syndrome nibbles.
+__host__ __device__ inline size_t soft_bytes(int n, int W) { return ((size_t)4 * n * W + 15) & ~(size_t)15; }
+
 // Threads: tid = ((row slot) * P + half) * W + w.  The two halves of a row sit
 // W lanes apart in one warp.
 template <int MAXH, int P, int W, bool TABLES, int MAXT>
@@ -51,7 +56,7 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
     const int n = A.n, m = A.m, Z = A.Z, Mb = A.Mb, nblk = A.nblk;
     const int tab_words = (int)ldpc_dev::tables_words(Mb, nblk);
     uint32_t* E_s = reinterpret_cast<uint32_t*>(smem);
-    int32_t* s_tab = reinterpret_cast<int32_t*>(smem + (size_t)4 * n * W);
+    int32_t* s_tab = reinterpret_cast<int32_t*>(smem + soft_bytes(n, W));
     uint8_t* syn_s = reinterpret_cast<uint8_t*>(s_tab + tab_words);
     __shared__ uint32_t s_bad[W], s_active[W];
     __shared__ int s_iters[4 * W];
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(MAXT) decode_kernel(DecodeArgs A) {
 
 inline size_t smem_bytes(const ldpc_code* c, int W) {
     const size_t tab_words = (size_t)((2 * c->Mb + 1 + 1) & ~1) + 2 * (size_t)c->nblk;
-    size_t b = (size_t)4 * c->n * W + sizeof(int32_t) * tab_words + (size_t)c->m * W;
+    size_t b = soft_bytes(c->n, W) + sizeof(int32_t) * tab_words + (size_t)c->m * W;
     return (b + 15) & ~(size_t)15;
 }
 

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
     const int tab_words = (int)ldpc_dev::tables_words(Mb, nblk);
     uint32_t* E_s = reinterpret_cast<uint32_t*>(smem);
     uint8_t* E_b = smem;
-    int32_t* s_tab = reinterpret_cast<int32_t*>(smem + (size_t)4 * n * W);
+    int32_t* s_tab = reinterpret_cast<int32_t*>(smem + soft_bytes(n, W));
     uint8_t* syn_s = reinterpret_cast<uint8_t*>(s_tab + tab_words);
     constexpr int NL = 4 * W;
     __shared__ int s_frame[NL], s_it[NL], s_mag[NL], s_ns[NL], s_np[NL];

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(512, 2) relaxed_forward_kernel(RelaxArgs A) {
     const int flq = q / RT, rr = q - flq * RT;
     const int fl = flq < FR ? flq : 0;
     float* E_s = fsm;
-    int32_t* s_tab = reinterpret_cast<int32_t*>(fsm + (size_t)FR * n);
+    int32_t* s_tab = reinterpret_cast<int32_t*>(fsm + (((size_t)FR * n + 3) & ~(size_t)3));  // 16-byte aligned (int2 entries)
     const ldpc_dev::Tables TB = ldpc_dev::load_tables(s_tab, A.tab, A.Mb, A.nblk, Z, 1, tid, T);
     const int64_t fbase = (int64_t)blockIdx.x * FR;
     const int64_t f = fbase + fl;
@@ -459,7 +459,7 @@ int ldpc_relaxed_forward(const ldpc_code* code, const float* llr, const uint8_t*
     if (loss) LDPC_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
     const Shape sh = cta_shape(c->Z);
     const int FR = sh.FR;
-    const size_t smem = sizeof(float) * (size_t)FR * c->n + tab_bytes(c);
+    const size_t smem = sizeof(float) * (((size_t)FR * c->n + 3) & ~(size_t)3) + tab_bytes(c);
     if ((int64_t)smem > ldpc::max_dyn_smem(c->device)) return fail(LDPC_EUNSUPPORTED, "relaxed forward: shared memory");
     RelaxArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, c->edges, llr, syn, bits, batch, iters, alpha, gamma,
                 layer_class, n_classes, kappa, ckE, ckL, loss, nullptr, nullptr, nullptr, nullptr, nullptr};

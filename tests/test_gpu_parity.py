@@ -248,3 +248,16 @@ def test_every_unroll_width_batch_and_persistent(dmax):
     bits, iters, ok = code.reconcile_persistent(_cuda(yb), _cuda(qv), _cuda(inputs.pack_bits(syn_u)), T)
     torch.cuda.synchronize()
     _assert_same((inputs.unpack_bits(bits.cpu().numpy(), code.n), iters.cpu().numpy(), ok.cpu().numpy()), o)
+
+
+@pytest.mark.parametrize("Z,Nb", [(7, 9), (13, 15), (5, 21)])
+def test_decode_odd_code_length(Z, Nb):
+    """n odd: the soft values take 4 n bytes per word of lanes, not a multiple
+    of 8, and the code tables behind them must still be aligned."""
+    base = inputs.qc_base_matrix(4, Nb, Z, 3, 60 + Z)
+    assert (Nb * Z) % 2 == 1
+    xa, yb = _frames(base, Z, 11, 0.04, 70 + Z)
+    llr, syn_u = _oracle_inputs(base, Z, xa, yb, 0.04)
+    for words in (1, 0):
+        g, o = _decode_both(base, Z, llr, syn_u, 20, words=words)
+        _assert_same(g, o)

@@ -126,3 +126,18 @@ def test_persistent_launch_captured_in_cuda_graph():
     torch.cuda.synchronize()
     for a, b in zip(ref, out):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("Z,Mb,Nb", [(7, 6, 19), (5, 7, 21)])
+def test_persistent_sizes_not_multiples_of_eight(Z, Mb, Nb):
+    """n and m not multiples of 8: the refill and the write-out take a byte of
+    variables (and of checks) per step and must stop at n (m)."""
+    case = _mixed_case(23, Z=Z, seed=40 + Z, Mb=Mb, Nb=Nb, f_target=1.6)
+    assert case["n"] % 8 and case["m"] % 8
+    code, bits, iters, ok = _run(case, 30)
+    ob, oi, oo, _ = orc.decode(case["base"], case["Z"], case["llr"], case["syn_u"], 30)
+    assert np.array_equal(ok, oo) and np.array_equal(iters, oi)
+    assert np.array_equal(inputs.unpack_bits(bits, case["n"]), ob)
+    # padding bits past n in the last output byte stay 0
+    pad = 8 * bits.shape[1] - case["n"]
+    assert np.all(bits[:, -1] >> (8 - pad) == 0)
