@@ -11,6 +11,7 @@ instances compile in parallel.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import re
@@ -87,9 +88,23 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Build the library unless it is up to date; returns its path.  Processes
+    that start together (ranks of one job, test workers) take a file lock, so
+    one of them compiles and the others find the library built."""
     if not force and up_to_date():
         return LIB_PATH
     os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():
+                return LIB_PATH
+            return _build_locked(verbose, extra)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, extra) -> str:
     cc = nvcc()
     objs = []
 
