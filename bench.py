@@ -185,18 +185,41 @@ def roofline_alu(it_sum, edges, seconds, clk):
             "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {float(mhz):.0f} MHz x 4 byte lanes"}
 
 
-def profiled_traffic(kernel: str, workload: str, launch_frames: int):
-    """DRAM bytes per launch from the committed ncu summary of the kernel, if
-    it was taken on the current kernel source; else None."""
+def profiled_traffic(kernel: str, workload: str, launch_frames: int, key: str = "dram_bytes_per_frame"):
+    """Bytes per launch from the committed ncu summary of the kernel (DRAM by
+    default, ``l2_bytes_per_frame`` for the L2 slices), if it was taken on the
+    current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     msha = re.search(r"kernel_sha:\s*([0-9a-f]+)", txt)
-    mtr = re.search(r"dram_bytes_per_frame:\s*([0-9.eE+]+)", txt)
+    mtr = re.search(key + r":\s*([0-9.eE+]+)", txt)
     if not msha or not mtr or msha.group(1) != kernel_sources_sha():
         return None
     return float(mtr.group(1)) * launch_frames
+
+
+def measure_l2_copy_gbs(dev, mbytes: int = 24, reps: int = 20) -> float:
+    """Copy bandwidth of a buffer that stays in L2 (bytes read + written per
+    second, best of five batches of ``reps`` copies, CUDA events): the L2
+    counterpart of the HBM copy peak, for kernels whose traffic L2 serves."""
+    import torch
+    a = torch.ones((mbytes << 20) // 4, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    st = torch.cuda.current_stream(dev)
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        best = max(best, 2.0 * a.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
 
 
 # ----------------------------------------------------------------- reference
@@ -460,6 +483,14 @@ def run_ours(args, rank, world, dist):
     if rank != 0:
         return
     traffic = profiled_traffic(kernel_name, w.name, B)
+    l2_traffic = profiled_traffic(kernel_name, w.name, B, "l2_bytes_per_frame")
+    l2 = None
+    if l2_traffic is not None:  # the messages are partly served from L2: its share against a measured L2 copy
+        l2_peak = measure_l2_copy_gbs(dev)
+        l2 = {"achieved": l2_traffic / dec_s / 1e9, "peak": l2_peak, "unit": "GB/s",
+              "frac": l2_traffic / dec_s / 1e9 / l2_peak, "traffic": l2_traffic,
+              "traffic_source": "lts__t_bytes.sum per launch, committed ncu summary of this kernel source",
+              "peak_kind": "measured in this run: device copy of a 24 MB buffer held in L2, best of 5 x 20"}
     line = {
         "metric": METRIC,
         "value": corr_tot / step_max / 1e6,
@@ -491,7 +522,7 @@ def run_ours(args, rank, world, dist):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": kernel_name, "kernel_ms": dec_s * 1e3,
-                     "algorithmic_bytes": alg_bytes},
+                     "algorithmic_bytes": alg_bytes, "l2": l2},
         "roofline_alu": roofline_alu(it_sum, code.edges, dec_s, clk),
         "e2e": {"value": e_tot / e2e_max / 1e6, "unit": "Mbps", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
