@@ -430,6 +430,23 @@ size_t tab_bytes(const ldpc_code* c) {
     return sizeof(int32_t) * ((size_t)((2 * c->Mb + 1 + 1) & ~1) + 2 * (size_t)c->nblk);
 }
 
+// Unroll width of the relaxation's kernels: the smallest of 6, 9, 12 and 16
+// slots that holds half the longest row (fewer idle slots and, in the
+// adjoint's five per-slot arrays, fewer registers).
+template <template <int> class K>
+auto pick_width(int max_deg) {
+    const int h = (max_deg + 1) / 2;
+    return h <= 6 ? K<6>::fn : h <= 9 ? K<9>::fn : h <= 12 ? K<12>::fn : K<16>::fn;
+}
+template <int H>
+struct ForwardK {
+    static constexpr auto fn = relaxed_forward_kernel<H>;
+};
+template <int H>
+struct BackwardK {
+    static constexpr auto fn = relaxed_backward_kernel<H>;
+};
+
 int check_common(const ldpc_code* c, int batch, int iters, int ncls, float kappa) {
     using ldpc::fail;
     if (!c) return fail(LDPC_EINVAL, "relaxed decoder: NULL code");
@@ -464,7 +481,7 @@ int ldpc_relaxed_forward(const ldpc_code* code, const float* llr, const uint8_t*
     RelaxArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, c->edges, llr, syn, bits, batch, iters, alpha, gamma,
                 layer_class, n_classes, kappa, ckE, ckL, loss, nullptr, nullptr, nullptr, nullptr, nullptr};
     const int grid = (batch + FR - 1) / FR;
-    auto kern = c->max_deg <= 24 ? relaxed_forward_kernel<12> : relaxed_forward_kernel<16>;
+    auto kern = pick_width<ForwardK>(c->max_deg);
     LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, sh.T, smem, st>>>(A);
     ldpc::count_launch();
@@ -496,7 +513,7 @@ int ldpc_relaxed_backward(const ldpc_code* code, const uint8_t* syn, const uint8
                 gamma, layer_class, n_classes, kappa, const_cast<float*>(ckE), const_cast<float*>(ckL), nullptr,
                 V, gL, grad_alpha, grad_gamma, grad_llr};
     const int grid = (batch + FR - 1) / FR;
-    auto kern = c->max_deg <= 24 ? relaxed_backward_kernel<12> : relaxed_backward_kernel<16>;
+    auto kern = pick_width<BackwardK>(c->max_deg);
     LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, sh.T, smem, st>>>(A);
     ldpc::count_launch();

@@ -138,3 +138,30 @@ def test_forward_and_gradient_on_special_shapes(case):
     ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
     got = np.concatenate([g_al.ravel(), g_ga.ravel()])
     assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("Nb", [18, 24, 32])
+def test_every_unroll_width_against_fp64(Nb):
+    """Rows of 18, 24 and 32 edges select the kernels unrolled for 9, 12 and
+    16 slots per half row (the other tests' codes take 6)."""
+    Mb, Z, B = 2, 8, 4
+    g = np.random.default_rng(Nb)
+    base = g.integers(0, Z, size=(Mb, Nb)).astype(np.int32)  # every block nonzero: row degree Nb
+    n = Nb * Z
+    xa = g.integers(0, 2, size=(B, n)).astype(np.uint8)
+    from oracle import core as orc
+    syn = orc.syndrome(base, Z, xa)
+    llr = ((1 - 2.0 * xa) * 3.0 + g.normal(0, 1.5, size=(B, n))).astype(np.float32)
+    T = 3
+    C = len(rx.degree_classes(base)[1])
+    al = g.uniform(0.7, 1.1, (T, C)).astype(np.float32).astype(np.float64)
+    ga = g.uniform(0.05, 0.3, (T, C)).astype(np.float32).astype(np.float64)
+    loss, E, g_al, g_ga, _, _ = _gpu(base, Z, llr, syn, xa, al, ga, 0.431, T)
+    E64 = rx.decode(base, Z, llr.astype(np.float64), syn, T, al, ga, kappa=0.431)
+    rel = np.abs(E - E64) / np.maximum(np.abs(E64), 1.0)
+    assert rel.max() <= 1e-4, rel.max()
+    l64, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=0.431)
+    assert abs(loss - l64) <= 1e-4 * abs(l64)
+    ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
+    got = np.concatenate([g_al.ravel(), g_ga.ravel()])
+    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
