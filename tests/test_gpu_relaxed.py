@@ -165,3 +165,23 @@ def test_every_unroll_width_against_fp64(Nb):
     ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
     got = np.concatenate([g_al.ravel(), g_ga.ravel()])
     assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
+
+
+def test_larger_code_two_frames_per_cta():
+    """n = 5120 at Z = 128: two frames per CTA, 83 KB of soft values and their
+    adjoints in shared memory, rows of up to 19 edges (the 12-slot kernels)."""
+    base, Z, llr, syn, xa = _case(Mb=8, Nb=40, Z=128, B=4, seed=11)
+    T = 3
+    C = len(rx.degree_classes(base)[1])
+    g = np.random.default_rng(12)
+    al = g.uniform(0.7, 1.1, (T, C)).astype(np.float32).astype(np.float64)
+    ga = g.uniform(0.05, 0.3, (T, C)).astype(np.float32).astype(np.float64)
+    loss, E, g_al, g_ga, _, _ = _gpu(base, Z, llr, syn, xa, al, ga, 0.431, T)
+    E64 = rx.decode(base, Z, llr.astype(np.float64), syn, T, al, ga, kappa=0.431)
+    rel = np.abs(E - E64) / np.maximum(np.abs(E64), 1.0)
+    assert rel.max() <= 1e-4, rel.max()
+    l64, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=0.431)
+    assert abs(loss - l64) <= 1e-4 * abs(l64)
+    ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
+    got = np.concatenate([g_al.ravel(), g_ga.ravel()])
+    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
