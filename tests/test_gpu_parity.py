@@ -225,7 +225,7 @@ def test_decode_is_deterministic_and_batch_independent():
         assert np.array_equal(a[13], b[0])
 
 
-@pytest.mark.parametrize("dmax", [3, 8, 12, 17, 19, 21, 23, 25, 27, 31, 45, 60])
+@pytest.mark.parametrize("dmax", [3, 8, 12, 17, 19, 21, 23, 25, 27, 31, 45, 60, 64])
 def test_every_unroll_width_batch_and_persistent(dmax):
     """Codes whose longest row lands on each compiled unroll width (and on
     the row sizes just below a width); rows of several degrees per code so
