@@ -40,7 +40,7 @@ struct PersistArgs {
     int32_t* out_iters;
     uint8_t* out_ok;
     uint32_t* msg;
-    int* queue;
+    int* queue;  // [0] frames claimed, [1] frames finished, [2..3] their iterations (64 bit); zeroed per launch
 };
 
 // Frame id of work-list slot `slot`, or -1 past the end of the list or for an
@@ -50,6 +50,12 @@ __device__ __forceinline__ int frame_of(const PersistArgs& A, int slot) {
     const int f = A.list ? A.list[slot] : slot;
     return (f >= 0 && f < A.batch) ? f : -1;
 }
+
+// The claim step's hold rule: only a frame past kHoldAfter iterations can
+// make its CTA hold, and only once kHoldMinDone frames have finished (for the
+// mean iteration count).
+constexpr int kHoldAfter = 16;
+constexpr int kHoldMinDone = 64;
 
 template <int MAXH, int P, int W, int MAXT>
 __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
@@ -272,16 +278,42 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
             A.out_ok[f] = s_okf[tid];
         }
         __syncthreads();
-        // ---- claim the next frames for the finished lanes
+        // ---- claim the next frames for the finished and the idle lanes.  A
+        // CTA whose oldest live frame is long past the typical count (almost
+        // surely one that runs to max_iter) holds instead -- claims nothing and
+        // leaves its free lanes idle -- when the frames left in the queue, at
+        // the mean iteration count of the finished ones and with half again as
+        // margin, fit in the lanes of the whole grid before that frame ends:
+        // it then spends its remaining iterations without refills, and the
+        // queue drains through the other CTAs no later than it would have.
         if (tid == 0) {
+            unsigned long long* done_iters = reinterpret_cast<unsigned long long*>(A.queue + 2);
+            int fin = 0;
+            unsigned long long fin_it = 0;
+            int oldest = 0;
+            for (int lane = 0; lane < NL; ++lane) {
+                if (s_done[lane]) {
+                    ++fin;
+                    fin_it += (unsigned)s_it[lane];
+                }
+                if ((s_active[lane >> 2] >> (8 * (lane & 3))) & 1u) oldest = max(oldest, s_it[lane]);
+            }
+            const int done_f = atomicAdd(A.queue + 1, fin) + fin;
+            const unsigned long long done_i = atomicAdd(done_iters, fin_it) + fin_it;
+            bool hold = false;
+            if (oldest >= kHoldAfter && done_f >= kHoldMinDone) {
+                const long long left = (long long)A.list_len - atomicAdd(A.queue, 0);
+                hold = left <= 0 || 3ull * (unsigned long long)left * done_i <
+                                        2ull * (unsigned long long)done_f * gridDim.x * NL * (A.max_iter - oldest);
+            }
             int k = 0;
-            for (int lane = 0; lane < NL; ++lane) k += s_done[lane];
-            const int base = atomicAdd(A.queue, k);
+            for (int lane = 0; lane < NL; ++lane) k += (s_done[lane] || s_frame[lane] < 0) ? 1 : 0;
+            const int base = hold ? 0 : atomicAdd(A.queue, k);
             int i = 0;
             for (int lane = 0; lane < NL; ++lane) {
-                if (!s_done[lane]) continue;
+                if (!s_done[lane] && s_frame[lane] >= 0) continue;  // still decoding
                 s_done[lane] = 0;
-                s_frame[lane] = frame_of(A, base + i++);
+                s_frame[lane] = hold ? -1 : frame_of(A, base + i++);
                 if (s_frame[lane] >= 0) {
                     s_load[lane >> 2] |= 0xFFu << (8 * (lane & 3));
                     s_any_load = 1;
@@ -313,7 +345,7 @@ int launch_p(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int* gri
     if (grid < 1) grid = 1;
     *grid_out = (int)grid;
     if (dry) return LDPC_OK;
-    LDPC_CUDA_TRY(cudaMemsetAsync(A.queue, 0, sizeof(int), st));
+    LDPC_CUDA_TRY(cudaMemsetAsync(A.queue, 0, 4 * sizeof(int), st));
     kern<<<(int)grid, T, smem, st>>>(A);
     ldpc::count_launch();
     LDPC_CUDA_TRY(cudaGetLastError());
