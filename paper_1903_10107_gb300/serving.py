@@ -62,6 +62,7 @@ class _Slot:
     event: object = None
     host_out: tuple = ()
     nbytes_held: int = 0
+    keep: tuple = ()        # device tensors of the launch in flight
 
 
 class CodeEntry:
@@ -162,7 +163,7 @@ class ReconciliationServer:
             r.bits = (bits[2 * i].copy(), bits[2 * i + 1].copy())
             r.t_done = now
         self.held -= slot.nbytes_held
-        slot.busy, slot.event, slot.host_out, slot.keep = [], None, (), None
+        slot.busy, slot.event, slot.host_out, slot.keep = [], None, (), ()
 
     # ------------------------------------------------------------ loop
     def serve(self, requests, realtime: bool = True):
