@@ -244,8 +244,10 @@ class InteractiveProtocol:
     did not match get more bits revealed -- first the punctured positions,
     which become shortened, then key positions in the same order -- and are
     decoded again, up to ``max_rounds`` extra rounds.  Each reveal adds
-    ``ceil(df * key_bits * h(q))`` bits, raising the frame's efficiency by
-    about ``df``.  The efficiency of a frame counts every revealed bit:
+    ``ceil(df * key_bits * h(q))`` bits.  While punctured positions remain
+    this raises the frame's efficiency by about ``df``; revealed key positions
+    leave the key instead of adding to the leak, which raises it by only about
+    ``f * df * h(q)``.  The efficiency of a frame counts every revealed bit:
     leak = m - p0 + revealed punctured bits, key = n - p0 - s0 - revealed
     key bits, f = leak / (key * h(q))."""
 
