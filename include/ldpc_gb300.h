@@ -144,7 +144,10 @@ int ldpc_decode_batch_words(const ldpc_code* code, const int8_t* llr_in, const u
  * pull frames from a device work counter (frames of different rates, QBERs
  * and iteration counts share the mother code; section 4.1).  Every byte lane
  * of a CTA decodes one frame at a time and, when the frame stops, takes the
- * next one, so uneven iteration counts leave no lane idle while work remains.
+ * next one, so uneven iteration counts do not hold the others back.  A CTA
+ * whose oldest frame has run far longer than the mean leaves its free lanes
+ * idle while the rest of the queue fits the other lanes before that frame
+ * ends (it then runs without refills); results do not depend on the schedule.
  *   bob_bits, qber, rank, n_short, n_punct, known : as in ldpc_llr_from_bsc,
  *       indexed by frame id.
  *   target_syndrome : device, uint8[batch][ceil(m/8)], indexed by frame id.
