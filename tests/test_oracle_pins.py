@@ -329,3 +329,26 @@ def test_position_rank_punctures_low_weight_first():
     st = rate.position_states(rk, 5, 3)
     assert (st == 2).sum() == 3 and (st == 1).sum() == 5
     assert (rk[st == 2].max() < rk[st == 1].min())
+
+
+def test_scale_offset_table_formula_through_the_decoder():
+    """A single check on two variables: each edge receives the other edge's
+    magnitude (degree 2: no box-plus at all), so one iteration from LLRs
+    (40, -25) leaves E_0 = 40 - t(25) and E_1 = -25 + t(40) with the syndrome
+    bit 0, the sign product negative and t(m) = clamp(((m s + 8) >> 4) - o, 0, 127)
+    (reading R9).  The decoded bits after one iteration follow t across its
+    rounding and its clamp at 0, for scales and offsets around each flip."""
+    base = np.array([[0, 0]], dtype=np.int32)
+    llr = np.array([[40, -25]], dtype=np.int8)
+    syn = np.zeros((1, 1), dtype=np.uint8)
+
+    def t(m, s, o):
+        return min(max(((m * s + 8) >> 4) - o, 0), 127)
+
+    for s in range(4, 33):
+        for o in range(-3, 45):
+            e0, e1 = 40 - t(25, s, o), -25 + t(40, s, o)
+            bits, iters, ok, _ = core.decode(base, 1, llr, syn, 1, scale_q4=np.array([[s]], np.uint8),
+                                            offset_q=np.array([[o]], np.int8))
+            assert list(bits[0]) == [int(e0 < 0), int(e1 < 0)], (s, o)
+            assert int(ok[0]) == int((e0 < 0) == (e1 < 0)) and iters[0] == 1
