@@ -61,7 +61,7 @@ def lib():
             L.orc_llr_frame.restype = None
             L.orc_cn_magnitudes.argtypes = [P, I, I, I, P]
             L.orc_cn_magnitudes.restype = None
-            L.orc_decode_batch.argtypes = [P, I, I, I, P, P, I, I, I, I, P, P, P, P, P, I]
+            L.orc_decode_batch.argtypes = [P, I, I, I, P, P, I, I, I, I, P, P, I, P, P, P, I]
             L.orc_num_cores.restype = I
             _lib = L
     return _lib
@@ -141,8 +141,14 @@ def llr_frames(y: np.ndarray, qber, state=None, known=None, scale: float = LLR_S
 
 
 def decode(base, Z: int, llr: np.ndarray, syn: np.ndarray, max_iter: int, *, msg_max: int = MSG_MAX,
-           fold_mode: int = FOLD_FORWARD_BACKWARD, scale_q4=None, offset_q=None, threads: int = 0):
+           fold_mode: int = FOLD_FORWARD_BACKWARD, scale_q4=None, offset_q=None, stall_window: int = 0,
+           threads: int = 0):
     """Decode a batch.  llr int8 [batch][n], syn unpacked [batch][m].
+
+    ``stall_window`` K > 0 also stops a frame, as a failure, once its count
+    of unsatisfied checks has set no new minimum for K iterations (the
+    minimum tracked from iteration 1, with the first iteration reaching it);
+    not part of the paper's decoder, which is K = 0.
 
     Returns (bits unpacked [batch][n], iters int32 [batch], ok uint8 [batch],
     threads used)."""
@@ -160,8 +166,8 @@ def decode(base, Z: int, llr: np.ndarray, syn: np.ndarray, max_iter: int, *, msg
     iters = np.zeros(B, dtype=np.int32)
     ok = np.zeros(B, dtype=np.uint8)
     used = lib().orc_decode_batch(_ptr(base), Mb, Nb, Z, _ptr(llr), _ptr(syn), B, int(max_iter), int(msg_max),
-                                  int(fold_mode), _ptr(sq), _ptr(oq), _ptr(bits), _ptr(iters), _ptr(ok),
-                                  int(threads))
+                                  int(fold_mode), _ptr(sq), _ptr(oq), int(stall_window), _ptr(bits),
+                                  _ptr(iters), _ptr(ok), int(threads))
     if used < 0:
         raise ValueError(f"oracle decode failed ({used})")
     return bits, iters, ok, used

@@ -15,7 +15,9 @@
  *     (section 3.2);
  *   - variable node: saturation-oriented update of Algorithm 2 (section 3.3);
  *   - stopping test: all parity checks tested with the latest E_j at the end
- *     of each iteration (section 2).
+ *     of each iteration (section 2); optionally a stall window K that also
+ *     stops, as a failure, a frame whose count of unsatisfied checks has set
+ *     no new minimum for K iterations (not in the paper; off by default).
  * Readings where the paper is silent (fold order, L_ji width, syndrome sign,
  * degree-1 rows, LLR scale, offset tables) are the ones listed in the design
  * notes; each is marked "Reading" below.
@@ -205,6 +207,7 @@ typedef struct {
     int max_iter, msg_max, fold_mode;
     const uint8_t* scale_q4; /* [max_iter][Mb] or NULL */
     const int8_t* offset_q;  /* [max_iter][Mb] or NULL */
+    int stall;               /* stall window K, 0 = off */
 } orc_opts;
 
 static int row_parity_ok(const orc_graph* g, const int8_t* E, const uint8_t* syn) {
@@ -216,14 +219,26 @@ static int row_parity_ok(const orc_graph* g, const int8_t* E, const uint8_t* syn
     return 1;
 }
 
+/* Number of parity checks the hard decisions E < 0 leave unsatisfied. */
+static int unsatisfied_checks(const orc_graph* g, const int8_t* E, const uint8_t* syn) {
+    int u = 0;
+    for (int c = 0; c < g->m; c++) {
+        int par = 0;
+        for (int32_t e = g->row_ptr[c]; e < g->row_ptr[c + 1]; e++) par ^= E[g->vn[e]] < 0;
+        u += par != (syn[c] & 1);
+    }
+    return u;
+}
+
 /* One frame: llr[n], syn[m] (unpacked) -> bits[n] (unpacked), iterations, ok. */
 static void decode_one(const orc_graph* g, const orc_opts* o, const int8_t* llr, const uint8_t* syn,
                        int8_t* E, int8_t* L, int* v, int* a, int* mag, uint8_t* bits, int32_t* iters,
                        uint8_t* ok) {
     for (int j = 0; j < g->n; j++) E[j] = llr[j];
     memset(L, 0, (size_t)g->edges);
-    int done = 0, t = 0;
-    for (t = 1; t <= o->max_iter && !done; t++) {
+    int done = 0, stalled = 0, t = 0;
+    int u_best = 0x7FFFFFFF, t_best = 0; /* stall rule: fewest unsatisfied checks so far, first reached at t_best */
+    for (t = 1; t <= o->max_iter; t++) {
         for (int i = 0; i < g->Mb; i++) {            /* Reading: one block row = one layer */
             for (int r = 0; r < g->Z; r++) {         /* rows of a layer share no VN */
                 int c = i * g->Z + r;
@@ -252,10 +267,22 @@ static void decode_one(const orc_graph* g, const orc_opts* o, const int8_t* llr,
                 }
             }
         }
-        if (row_parity_ok(g, E, syn)) done = 1;      /* stopping test at the end of the iteration */
+        /* stopping test at the end of the iteration (section 2) */
+        if (o->stall > 0) {
+            /* Stall rule (not in the paper; off unless asked for): a frame whose
+             * count of unsatisfied checks has set no new minimum for K
+             * iterations stops as a failure. */
+            int u = unsatisfied_checks(g, E, syn);
+            if (u == 0) { done = 1; break; }
+            if (u < u_best) { u_best = u; t_best = t; }
+            else if (t - t_best >= o->stall) { stalled = 1; break; }
+        } else if (row_parity_ok(g, E, syn)) {
+            done = 1;
+            break;
+        }
     }
     for (int j = 0; j < g->n; j++) bits[j] = E[j] < 0; /* Reading: E = 0 decides 0 */
-    *iters = done ? t - 1 : o->max_iter;
+    *iters = (done || stalled) ? t : o->max_iter;
     *ok = (uint8_t)done;
 }
 
@@ -299,15 +326,16 @@ int orc_num_cores(void) {
 }
 
 /* Decode a batch: llr[batch][n] int8, syn[batch][m] unpacked -> bits[batch][n]
- * unpacked, iters[batch], ok[batch].  threads <= 0 uses every online core.
+ * unpacked, iters[batch], ok[batch].  stall = K > 0 enables the stall rule.
+ * threads <= 0 uses every online core.
  * Returns the number of threads used, or a negative value on error. */
 int orc_decode_batch(const int32_t* base, int Mb, int Nb, int Z, const int8_t* llr, const uint8_t* syn,
                      int batch, int max_iter, int msg_max, int fold_mode, const uint8_t* scale_q4,
-                     const int8_t* offset_q, uint8_t* bits, int32_t* iters, uint8_t* ok, int threads) {
+                     const int8_t* offset_q, int stall, uint8_t* bits, int32_t* iters, uint8_t* ok, int threads) {
     orc_graph g;
-    if (Mb <= 0 || Nb <= 0 || Z <= 0 || batch < 0 || max_iter < 1) return -1;
+    if (Mb <= 0 || Nb <= 0 || Z <= 0 || batch < 0 || max_iter < 1 || stall < 0) return -1;
     if (build_graph(base, Mb, Nb, Z, &g)) return -2;
-    orc_opts o = {max_iter, msg_max, fold_mode, scale_q4, offset_q};
+    orc_opts o = {max_iter, msg_max, fold_mode, scale_q4, offset_q, stall};
     if (threads <= 0) threads = orc_num_cores();
     if (threads > batch) threads = batch > 0 ? batch : 1;
     pthread_mutex_t mu = PTHREAD_MUTEX_INITIALIZER;

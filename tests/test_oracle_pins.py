@@ -352,3 +352,53 @@ def test_scale_offset_table_formula_through_the_decoder():
                                             offset_q=np.array([[o]], np.int8))
             assert list(bits[0]) == [int(e0 < 0), int(e1 < 0)], (s, o)
             assert int(ok[0]) == int((e0 < 0) == (e1 < 0)) and iters[0] == 1
+
+
+# ------------------------------------------------------------- stall rule
+
+def _stop_iteration(u, K, max_iter):
+    """Where the stall rule stops, by its definition, given the unsatisfied
+    counts u[t-1] after each iteration t of the plain decoder."""
+    best, t_best = None, 0
+    for t in range(1, max_iter + 1):
+        ut = int(u[t - 1])
+        if ut == 0:
+            return t, True
+        if best is None or ut < best:
+            best, t_best = ut, t
+        elif t - t_best >= K:
+            return t, False
+    return max_iter, False
+
+
+def test_stall_rule_truncates_the_plain_trajectory():
+    """The stall rule changes no decoding step, only where it stops: with
+    window K the oracle must return the plain decoder's state after the
+    iteration the rule's definition picks from the counts of unsatisfied
+    checks (taken here from the plain decoder's hard decisions after each
+    iteration, stopped there by max_iter, and the dense H)."""
+    base, Z = _small_code(21, Mb=8, Nb=32, Z=16)
+    H = tiny.dense_h(base, Z).astype(np.int64)
+    xa, yb = _frames(base, Z, 24, 0.075, 9)
+    syn = core.syndrome(base, Z, xa)
+    llr = core.llr_frames(yb, 0.075)
+    T = 40
+    # the plain decoder's hard decisions after t iterations, for every t
+    traj = []
+    for t in range(1, T + 1):
+        b, it, ok, _ = core.decode(base, Z, llr, syn, t)
+        traj.append(b)
+    u = np.stack([((b.astype(np.int64) @ H.T) % 2 != syn).sum(axis=1) for b in traj], axis=1)  # [frame][t-1]
+    stops = set()
+    for K in (1, 3, 6, 12, 41):
+        bits, iters, ok, _ = core.decode(base, Z, llr, syn, T, stall_window=K)
+        for f in range(len(llr)):
+            t_stop, success = _stop_iteration(u[f], K, T)
+            assert iters[f] == t_stop and bool(ok[f]) == success, (K, f)
+            assert np.array_equal(bits[f], traj[t_stop - 1][f])
+            stops.add((K, t_stop < T and not success))
+    assert (1, True) in stops and (41, True) not in stops  # both stall stops and none occurred
+    # a window longer than the cap is the plain decoder
+    b0, i0, o0, _ = core.decode(base, Z, llr, syn, T)
+    b1, i1, o1, _ = core.decode(base, Z, llr, syn, T, stall_window=T)
+    assert np.array_equal(b0, b1) and np.array_equal(i0, i1) and np.array_equal(o0, o1)
