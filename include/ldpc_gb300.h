@@ -72,24 +72,34 @@ int ldpc_code_info(const ldpc_code* code, int* n, int* m, int64_t* edges, int* m
  * graph).  Synchronous. */
 int ldpc_code_reserve(ldpc_code* code, int batch);
 
-/* Channel LLRs of section 3.1 for a binary symmetric channel, quantised to
- * int8: for a key position, round-half-away(ln((1-q_f)/q_f) * scale) clamped
- * to 127, positive for a received 0; punctured positions 0; shortened
- * positions +127 (known bit 0) or -127 (known bit 1).  Rate adaptation of
- * section 4.1: with `rank` given, position j of frame f is shortened when
- * rank[j] < n_short[f], punctured when n_short[f] <= rank[j] <
+/* Per-frame channel LLR magnitude of section 3.1 for a binary symmetric
+ * channel, computed on the host: mag[f] = round-half-away(ln((1-q_f)/q_f) *
+ * scale), clamped to 127.  Host code with the host C library's log, so that
+ * every caller on one machine (and the reference CPU decoder) gets the same
+ * integer even where the product lands next to a half-integer; the kernels
+ * take these magnitudes instead of evaluating the logarithm on the device.
+ *   qber    : host, double[batch] per-frame QBER in (0, 0.5).
+ *   scale   : LSB per nat (> 0).
+ *   mag_out : host, int8[batch].
+ * Errors: LDPC_EINVAL (NULL, scale <= 0, a QBER outside (0, 0.5)). */
+int ldpc_llr_magnitudes(const double* qber, int batch, double scale, int8_t* mag_out);
+
+/* Channel LLRs of section 3.1, quantised to int8: a key position gets
+ * +llr_mag[f] for a received 0 and -llr_mag[f] for a 1; punctured positions
+ * 0; shortened positions +127 (known bit 0) or -127 (known bit 1).  Rate
+ * adaptation of section 4.1: with `rank` given, position j of frame f is
+ * shortened when rank[j] < n_short[f], punctured when n_short[f] <= rank[j] <
  * n_short[f] + n_punct[f], a key bit otherwise.
  *   bob_bits : device, uint8[batch][ceil(n/8)] Bob's key.
- *   qber     : device, double[batch] per-frame QBER in (0, 0.5).
+ *   llr_mag  : device, int8[batch] per-frame magnitudes (ldpc_llr_magnitudes).
  *   rank     : device, int32[n] puncturing order, or NULL (all key bits).
  *   n_short, n_punct : device, int32[batch], or NULL (zero).
  *   known    : device, uint8[batch][ceil(n/8)] values of shortened positions
  *              (only those positions are read), or NULL when n_short is NULL.
- *   scale    : LSB per nat (8.0 for the workloads of this library).
- *   llr_out  : device, int8[batch][n]. */
-int ldpc_llr_from_bsc(const ldpc_code* code, const uint8_t* bob_bits, const double* qber, const int32_t* rank,
+ *   llr_out  : device, int8[batch][n].  batch <= 65535. */
+int ldpc_llr_from_bsc(const ldpc_code* code, const uint8_t* bob_bits, const int8_t* llr_mag, const int32_t* rank,
                       const int32_t* n_short, const int32_t* n_punct, const uint8_t* known, int batch,
-                      double scale, int8_t* llr_out, void* stream);
+                      int8_t* llr_out, void* stream);
 
 /* Syndrome s = H x (mod 2) of a batch of packed bit vectors: the message
  * Alice sends in the syndrome-based protocol (section 4.1).
@@ -148,33 +158,75 @@ int ldpc_decode_batch_words(const ldpc_code* code, const int8_t* llr_in, const u
  * whose oldest frame has run far longer than the mean leaves its free lanes
  * idle while the rest of the queue fits the other lanes before that frame
  * ends (it then runs without refills); results do not depend on the schedule.
- *   bob_bits, qber, rank, n_short, n_punct, known : as in ldpc_llr_from_bsc,
- *       indexed by frame id.
+ *   bob_bits, llr_mag, rank, n_short, n_punct, known : as in
+ *       ldpc_llr_from_bsc, indexed by frame id.
  *   target_syndrome : device, uint8[batch][ceil(m/8)], indexed by frame id.
  *   batch : number of frames in the per-frame arrays.
  *   frame_list : device, int32[list_len] frame ids to decode (e.g. the frames
  *       still failing after an interactive reveal), or NULL for 0..list_len-1
  *       (then list_len <= batch).  Ids outside [0, batch) are skipped.
- *   max_iter, llr_scale : iteration cap and LSB per nat.
+ *   max_iter : iteration cap.
+ *   stall_window : K >= 0.  With K > 0 a frame also stops, as a failure,
+ *       after iteration t when its number of unsatisfied parity checks has
+ *       set no new minimum since iteration t - K (the minimum and the
+ *       iteration that first reached it are tracked per frame from iteration
+ *       1).  K = 0 is the plain decoder: it stops only at a syndrome match or
+ *       max_iter.  Not in the paper: a stopping criterion for frames that
+ *       have stopped converging (they would run to max_iter), in the spirit
+ *       of the paper's remark that early termination adds throughput; the
+ *       reference CPU decoder implements the same rule.  Needs m <= 65535.
  *   words : 32-bit lane words per CTA (1, 2, 4; 0 = automatic).
  *   ctas_per_sm : resident CTAs per SM (0 = as many as fit).
+ *   threads : threads per CTA (0 = one thread pair per check row of a
+ *       layer, at most 1024 (512 for rows of more than 32 edges)); otherwise
+ *       a multiple of 32*words no larger than that, each thread pair then
+ *       taking several rows of a layer.  Results do not depend on it.
  *   out_bits, out_iters, out_ok : device, indexed by frame id; entries of
  *       frames not in the list are left untouched.
  * Per-frame results equal ldpc_decode_batch on the LLRs of
  * ldpc_llr_from_bsc.  Capturable in a CUDA graph once the scratch arena is
  * large enough (ldpc_code_reserve_persistent). */
-int ldpc_reconcile_persistent(const ldpc_code* code, const uint8_t* bob_bits, const double* qber,
+int ldpc_reconcile_persistent(const ldpc_code* code, const uint8_t* bob_bits, const int8_t* llr_mag,
                               const int32_t* rank, const int32_t* n_short, const int32_t* n_punct,
                               const uint8_t* known, const uint8_t* target_syndrome, int batch,
-                              const int32_t* frame_list, int list_len, int max_iter, double llr_scale, int words,
-                              int ctas_per_sm, uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok,
-                              void* stream);
+                              const int32_t* frame_list, int list_len, int max_iter, int stall_window,
+                              int words, int ctas_per_sm, int threads, uint8_t* out_bits, int32_t* out_iters,
+                              uint8_t* out_ok, void* stream);
+
+/* The interactive rate-adaptive protocol of sections 4.1 and 4.2 in one
+ * persistent launch: ldpc_reconcile_persistent, where a frame whose decode
+ * fails (no syndrome match by max_iter, or the stall rule) and has rounds
+ * left is rebuilt in its lane at the next round's state -- more of its
+ * puncturing order revealed by Alice, punctured positions first, every
+ * revealed position then shortened with her value -- and decoded again from
+ * its channel LLRs.  Rounds of different frames overlap; no round waits for
+ * the slowest frame of the one before.  Per-frame results equal decoding
+ * each round separately (ldpc_reconcile_persistent with the round's
+ * counts), round after round, until a match or the last round.
+ *   n_short, n_punct : device, int32[batch] the counts of round 0 (the rate
+ *       plan for the starting efficiency).  In round r frame f has
+ *       n_short[f] + R and max(n_punct[f] - R, 0) of them, R = reveal[f][r].
+ *   reveal : device, int32[batch][max_rounds + 1] cumulative revealed counts,
+ *       reveal[f][0] = 0, non-decreasing, R <= n - n_short[f]; the paper
+ *       does not fix how many bits a round reveals, the caller chooses.
+ *   max_rounds : rounds after the first (>= 0).
+ *   out_iters : iterations summed over the frame's rounds.
+ *   out_rounds : device, int32[batch] index of the frame's last round.
+ *   rank, known are required; the other arguments as in
+ *   ldpc_reconcile_persistent. */
+int ldpc_reconcile_interactive(const ldpc_code* code, const uint8_t* bob_bits, const int8_t* llr_mag,
+                               const int32_t* rank, const int32_t* n_short, const int32_t* n_punct,
+                               const uint8_t* known, const uint8_t* target_syndrome, int batch,
+                               const int32_t* frame_list, int list_len, int max_iter, int stall_window,
+                               const int32_t* reveal, int max_rounds, int words, int ctas_per_sm, int threads,
+                               uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, int32_t* out_rounds,
+                               void* stream);
 
 /* Grow the scratch arena now for a persistent decode of `list_len` frames
- * with the given `words` and `ctas_per_sm` (0 = automatic, as in
+ * with the given `words`, `ctas_per_sm` and `threads` (0 = automatic, as in
  * ldpc_reconcile_persistent), so that the decode itself allocates nothing
  * and can be captured in a CUDA graph.  Synchronous. */
-int ldpc_code_reserve_persistent(ldpc_code* code, int list_len, int words, int ctas_per_sm);
+int ldpc_code_reserve_persistent(ldpc_code* code, int list_len, int words, int ctas_per_sm, int threads);
 
 /* FP32 relaxation of the layered decoder, for learning check-node
  * corrections (the normalised/offset forms section 2 lists as alternatives).
@@ -239,10 +291,12 @@ int ldpc_relaxed_backward(const ldpc_code* code, const uint8_t* syn, const uint8
  *     them into several calls.
  *   - The array exists on every GPU that loads the library and stays there
  *     until the process exits.
- *   - Set-up: the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current and caches it; make
- *     the first call before any stream capture.  The code's device must be
- *     the current device (else LDPC_EINVAL).
+ *   - Set-up: the first call in a CUDA context (per device, and again after
+ *     cudaDeviceReset or in a caller-created context) looks up the array's
+ *     device address there (cudaGetSymbolAddress, which also loads the
+ *     library's module into that context) and caches it by the context's
+ *     id; make that first call before any stream capture.  The code's device
+ *     must be the current device (else LDPC_EINVAL).
  *   - All calls share the one array, which keeps the previous call's
  *     contents.  Nothing needs clearing (the decoder never reads a message it
  *     has not written in the same call), but two calls whose kernels overlap

@@ -42,8 +42,8 @@ _GEN_TEMPLATE = """// Written by build.py: the batch and persistent decoders of 
 
 template int ldpc_dec::decode_launch<{m}>(const ldpc_code*, const ldpc_dec::DecodeArgs&, int, int, bool,
                                           cudaStream_t);
-template int ldpc_dec::persist_launch<{m}>(const ldpc_code*, const ldpc_dec::PersistArgs&, int, int, int*, bool,
-                                           cudaStream_t);
+template int ldpc_dec::persist_launch<{m}>(const ldpc_code*, const ldpc_dec::PersistArgs&, int, int, int, int*,
+                                           bool, cudaStream_t);
 """
 
 

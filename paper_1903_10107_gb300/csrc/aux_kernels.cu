@@ -1,6 +1,9 @@
 // Channel-LLR quantisation (section 3.1 with the rate adaptation of section
 // 4.1), syndrome computation (section 4.1 protocol) and a table probe of the
-// byte-lane check-node arithmetic.
+// byte-lane check-node arithmetic.  The per-frame LLR magnitude is computed
+// on the host (ldpc_llr_magnitudes, the host C library's log) and passed to
+// the kernels as int8, so the device never evaluates a transcendental whose
+// last-ulp rounding could differ from the host's at a half-integer.
 #include <math.h>
 
 #include "common.cuh"
@@ -11,14 +14,13 @@ constexpr int kLlrThreads = 256;
 
 // One thread per 8 positions of one frame (one byte of Bob's packed key).
 __global__ void __launch_bounds__(kLlrThreads)
-llr_kernel(const uint8_t* __restrict__ bob, const double* __restrict__ qber, const int32_t* __restrict__ rank,
+llr_kernel(const uint8_t* __restrict__ bob, const int8_t* __restrict__ llr_mag, const int32_t* __restrict__ rank,
            const int32_t* __restrict__ n_short, const int32_t* __restrict__ n_punct,
-           const uint8_t* __restrict__ known, int n, int nbytes, double scale, int8_t* __restrict__ out) {
+           const uint8_t* __restrict__ known, int n, int nbytes, int8_t* __restrict__ out) {
     const int f = blockIdx.y;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbytes) return;
-    const double q = qber[f];
-    long mag = lround(log((1.0 - q) / q) * scale);
+    int mag = llr_mag[f];
     mag = mag > 127 ? 127 : (mag < -127 ? -127 : mag);
     const int ns = n_short ? n_short[f] : 0;
     const int np = n_punct ? n_punct[f] : 0;
@@ -29,7 +31,7 @@ llr_kernel(const uint8_t* __restrict__ bob, const double* __restrict__ qber, con
     uint8_t v[8];
 #pragma unroll
     for (int q8 = 0; q8 < 8; q8++) {
-        int x = ((y >> q8) & 1) ? -(int)mag : (int)mag;
+        int x = ((y >> q8) & 1) ? -mag : mag;
         if (rank && q8 < jmax) {
             const int rk = rank[b * 8 + q8];
             if (rk < ns) x = ((kn >> q8) & 1) ? -127 : 127;
@@ -95,21 +97,36 @@ __global__ void tau_table_kernel(uint8_t* out) {
 
 extern "C" {
 
-int ldpc_llr_from_bsc(const ldpc_code* c, const uint8_t* bob_bits, const double* qber, const int32_t* rank,
+int ldpc_llr_magnitudes(const double* qber, int batch, double scale, int8_t* mag_out) {
+    using ldpc::fail;
+    if (batch < 0) return fail(LDPC_EINVAL, "ldpc_llr_magnitudes: negative batch");
+    if (batch == 0) return LDPC_OK;
+    if (!qber || !mag_out) return fail(LDPC_EINVAL, "ldpc_llr_magnitudes: NULL buffer");
+    if (!(scale > 0.0)) return fail(LDPC_EINVAL, "ldpc_llr_magnitudes: bad scale");
+    for (int f = 0; f < batch; ++f) {
+        const double q = qber[f];
+        if (!(q > 0.0 && q < 0.5)) return fail(LDPC_EINVAL, "ldpc_llr_magnitudes: QBER outside (0, 0.5)");
+        long r = lround(log((1.0 - q) / q) * scale);  // host libm, round half away from zero
+        mag_out[f] = (int8_t)(r > 127 ? 127 : r);
+    }
+    return LDPC_OK;
+}
+
+int ldpc_llr_from_bsc(const ldpc_code* c, const uint8_t* bob_bits, const int8_t* llr_mag, const int32_t* rank,
                       const int32_t* n_short, const int32_t* n_punct, const uint8_t* known, int batch,
-                      double scale, int8_t* llr_out, void* stream) {
+                      int8_t* llr_out, void* stream) {
     using ldpc::fail;
     if (!c) return fail(LDPC_EINVAL, "ldpc_llr_from_bsc: NULL code");
     if (batch < 0) return fail(LDPC_EINVAL, "ldpc_llr_from_bsc: negative batch");
     if (batch == 0) return LDPC_OK;
-    if (!bob_bits || !qber || !llr_out) return fail(LDPC_EINVAL, "ldpc_llr_from_bsc: NULL buffer");
+    if (!bob_bits || !llr_mag || !llr_out) return fail(LDPC_EINVAL, "ldpc_llr_from_bsc: NULL buffer");
     if (n_short && !known) return fail(LDPC_EINVAL, "ldpc_llr_from_bsc: shortening needs known values");
     if ((n_short || n_punct) && !rank) return fail(LDPC_EINVAL, "ldpc_llr_from_bsc: counts need a rank table");
-    if (!(scale > 0.0) || batch > 65535) return fail(LDPC_EINVAL, "ldpc_llr_from_bsc: bad scale or batch");
+    if (batch > 65535) return fail(LDPC_EINVAL, "ldpc_llr_from_bsc: batch above 65535");
     const int nbytes = (c->n + 7) / 8;
     dim3 grid((nbytes + kLlrThreads - 1) / kLlrThreads, batch);
-    llr_kernel<<<grid, kLlrThreads, 0, (cudaStream_t)stream>>>(bob_bits, qber, rank, n_short, n_punct, known,
-                                                                c->n, nbytes, scale, llr_out);
+    llr_kernel<<<grid, kLlrThreads, 0, (cudaStream_t)stream>>>(bob_bits, llr_mag, rank, n_short, n_punct, known,
+                                                                c->n, nbytes, llr_out);
     ldpc::count_launch();
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;

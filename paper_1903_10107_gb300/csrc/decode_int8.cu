@@ -77,22 +77,73 @@ namespace {
 constexpr size_t kStaticMsgBytes = (size_t)32 << 20;  // 32 MiB of message scratch
 __device__ __align__(256) uint32_t g_static_msg[kStaticMsgBytes / sizeof(uint32_t)];
 
-constexpr int kMaxDevices = 64;
+// Cached device addresses of g_static_msg, one per CUDA context.  A context
+// is identified by the driver's context id, which is never reused within a
+// process: after cudaDeviceReset the primary context is created anew (and
+// the library's module loaded again, possibly at another address), and a
+// caller's own non-primary context on the same device is another context,
+// so neither can pick up a stale address.
+struct StaticAddr {
+    unsigned long long ctx_id;
+    uint32_t* addr;
+};
+constexpr int kAddrSlots = 64;
 std::mutex g_static_mu;
-uint32_t* g_static_addr[kMaxDevices] = {};
+StaticAddr g_static_addr[kAddrSlots] = {};
+int g_static_next = 0;
 
-// Device address of g_static_msg on `device`, looked up once per device with
-// that device current (host code only knows the array's host-side stand-in).
-int static_msg_address(int device, uint32_t** out) {
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (device < 0 || device >= kMaxDevices) return ldpc::fail(LDPC_EUNSUPPORTED, "noalloc decode: device id");
-    if (!g_static_addr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_msg);
-        if (e != cudaSuccess) return ldpc::cuda_fail(e, "noalloc decode: cudaGetSymbolAddress");
-        g_static_addr[device] = static_cast<uint32_t*>(p);
+// Driver entry points, resolved through the runtime (the library does not
+// link the driver library itself).
+typedef int (*ctx_get_current_fn)(void** ctx);
+typedef int (*ctx_get_id_fn)(void* ctx, unsigned long long* id);
+
+// Id of the calling thread's current context, or 0 if there is none yet
+// (the runtime creates and binds it lazily) or the driver lacks the query.
+unsigned long long current_context_id() {
+    static ctx_get_current_fn get_cur = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult st;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &st) == cudaSuccess &&
+            st == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<ctx_get_current_fn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &st) == cudaSuccess &&
+            st == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<ctx_get_id_fn>(f);
+        resolved = true;
     }
-    *out = g_static_addr[device];
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_static_msg in the current context.  Host code only
+// knows the array's host-side stand-in; the address is looked up with
+// cudaGetSymbolAddress once per context (the first call in a context also
+// loads the library's module there) and cached by context id.
+int static_msg_address(uint32_t** out) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    unsigned long long id = current_context_id();
+    if (id) {
+        for (const StaticAddr& e : g_static_addr)
+            if (e.ctx_id == id) {
+                *out = e.addr;
+                return LDPC_OK;
+            }
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_msg);
+    if (e != cudaSuccess) return ldpc::cuda_fail(e, "noalloc decode: cudaGetSymbolAddress");
+    if (!id) id = current_context_id();  // the lookup has made the context current
+    if (id) {
+        g_static_addr[g_static_next] = StaticAddr{id, static_cast<uint32_t*>(p)};
+        g_static_next = (g_static_next + 1) % kAddrSlots;
+    }
+    *out = static_cast<uint32_t*>(p);
     return LDPC_OK;
 }
 
@@ -157,7 +208,7 @@ int ldpc_decode_batch_noalloc(const ldpc_code* code, const int8_t* llr_in, const
                                      " bytes of message scratch; the fixed scratch holds " +
                                      std::to_string(kStaticMsgBytes) + " bytes (decode fewer frames per call)");
     uint32_t* msg = nullptr;
-    int rc = static_msg_address(c->device, &msg);
+    int rc = static_msg_address(&msg);
     if (rc) return rc;
     DecodeArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, llr_in, target_syndrome, batch, max_iter, nullptr,
                  nullptr, out_bits, out_iters, out_ok, msg};

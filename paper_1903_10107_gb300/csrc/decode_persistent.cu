@@ -8,12 +8,12 @@ namespace {
 using ldpc_dec::PersistArgs;
 using ldpc_dec::smem_bytes;
 
-int dispatch(const ldpc_code* c, const PersistArgs& A, int W, int ctas_per_sm, int* grid, bool dry,
+int dispatch(const ldpc_code* c, const PersistArgs& A, int W, int ctas_per_sm, int threads, int* grid, bool dry,
              cudaStream_t st) {
     switch (ldpc_dec::pick_maxh(c->max_deg)) {
 #define LDPC_PERSIST_CASE(M) \
     case M:                  \
-        return ldpc_dec::persist_launch<M>(c, A, W, ctas_per_sm, grid, dry, st);
+        return ldpc_dec::persist_launch<M>(c, A, W, ctas_per_sm, threads, grid, dry, st);
         LDPC_MAXH_LIST(LDPC_PERSIST_CASE)
 #undef LDPC_PERSIST_CASE
         default:
@@ -25,7 +25,7 @@ int dispatch(const ldpc_code* c, const PersistArgs& A, int W, int ctas_per_sm, i
 
 extern "C" {
 
-int ldpc_code_reserve_persistent(ldpc_code* code, int list_len, int words, int ctas_per_sm) {
+int ldpc_code_reserve_persistent(ldpc_code* code, int list_len, int words, int ctas_per_sm, int threads) {
     if (!code || list_len < 0) return ldpc::fail(LDPC_EINVAL, "ldpc_code_reserve_persistent: bad argument");
     if (list_len == 0) return LDPC_OK;
     const int W = words > 0 ? words : 1;
@@ -33,29 +33,33 @@ int ldpc_code_reserve_persistent(ldpc_code* code, int list_len, int words, int c
     PersistArgs A{};
     A.list_len = list_len;
     int grid = 0;
-    int rc = dispatch(code, A, W, ctas_per_sm, &grid, true, nullptr);
+    int rc = dispatch(code, A, W, ctas_per_sm, threads, &grid, true, nullptr);
     if (rc) return rc;
     return ldpc::ensure_arena(code, (size_t)grid * 4 * W * (size_t)code->edges);
 }
 
-int ldpc_reconcile_persistent(const ldpc_code* code, const uint8_t* bob_bits, const double* qber,
-                              const int32_t* rank, const int32_t* n_short, const int32_t* n_punct,
-                              const uint8_t* known, const uint8_t* target_syndrome, int batch,
-                              const int32_t* frame_list, int list_len, int max_iter, double llr_scale, int words,
-                              int ctas_per_sm, uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok,
-                              void* stream) {
+}  // extern "C"
+
+namespace {
+
+int reconcile_common(const ldpc_code* c, const uint8_t* bob_bits, const int8_t* llr_mag, const int32_t* rank,
+                     const int32_t* n_short, const int32_t* n_punct, const uint8_t* known,
+                     const uint8_t* target_syndrome, int batch, const int32_t* frame_list, int list_len, int max_iter,
+                     int stall_window, const int32_t* reveal, int max_rounds, int words, int ctas_per_sm,
+                     int threads, uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, int32_t* out_rounds,
+                     void* stream) {
     using ldpc::fail;
-    const ldpc_code* c = code;
     if (!c) return fail(LDPC_EINVAL, "persistent decode: NULL code");
-    if (list_len < 0 || batch < 0 || max_iter < 1)
-        return fail(LDPC_EINVAL, "persistent decode: bad batch, list length or max_iter");
+    if (list_len < 0 || batch < 0 || max_iter < 1 || stall_window < 0)
+        return fail(LDPC_EINVAL, "persistent decode: bad batch, list length, max_iter or stall window");
+    if (stall_window > 0 && c->m > 0xFFFF)
+        return fail(LDPC_EUNSUPPORTED, "persistent decode: the stall window counts checks in 16 bits (m <= 65535)");
     if (!frame_list && list_len > batch) return fail(LDPC_EINVAL, "persistent decode: list_len > batch");
     if (list_len == 0) return LDPC_OK;
-    if (!bob_bits || !qber || !target_syndrome || !out_bits || !out_iters || !out_ok)
+    if (!bob_bits || !llr_mag || !target_syndrome || !out_bits || !out_iters || !out_ok)
         return fail(LDPC_EINVAL, "persistent decode: NULL buffer");
     if ((n_short || n_punct) && !rank) return fail(LDPC_EINVAL, "persistent decode: counts need a rank table");
     if (n_short && !known) return fail(LDPC_EINVAL, "persistent decode: shortening needs known values");
-    if (!(llr_scale > 0.0)) return fail(LDPC_EINVAL, "persistent decode: bad LLR scale");
     const int smem_limit = ldpc::max_dyn_smem(c->device);
     int W = words;
     if (W == 0) {
@@ -70,17 +74,72 @@ int ldpc_reconcile_persistent(const ldpc_code* code, const uint8_t* bob_bits, co
     }
     if ((W != 1 && W != 2 && W != 4) || (int64_t)smem_bytes(c, W) > smem_limit)
         return fail(LDPC_EINVAL, "persistent decode: unsupported words per row");
-    PersistArgs A{c->d_tab, c->Mb, c->nblk, c->Z, c->n, c->m, bob_bits, qber, rank, n_short, n_punct, known,
-                  target_syndrome, frame_list, batch, list_len, max_iter, llr_scale, out_bits, out_iters, out_ok,
-                  nullptr, c->d_queue};
+    PersistArgs A{};
+    A.tab = c->d_tab;
+    A.Mb = c->Mb;
+    A.nblk = c->nblk;
+    A.Z = c->Z;
+    A.n = c->n;
+    A.m = c->m;
+    A.bob = bob_bits;
+    A.mag = llr_mag;
+    A.rank = rank;
+    A.n_short = n_short;
+    A.n_punct = n_punct;
+    A.known = known;
+    A.syn = target_syndrome;
+    A.list = frame_list;
+    A.batch = batch;
+    A.list_len = list_len;
+    A.max_iter = max_iter;
+    A.stall = stall_window;
+    A.out_bits = out_bits;
+    A.out_iters = out_iters;
+    A.out_ok = out_ok;
+    A.reveal = reveal;
+    A.max_rounds = reveal ? max_rounds : 0;
+    A.out_rounds = out_rounds;
+    A.queue = c->d_queue;
     int grid = 0;
-    int rc = dispatch(c, A, W, ctas_per_sm, &grid, true, (cudaStream_t)stream);
+    int rc = dispatch(c, A, W, ctas_per_sm, threads, &grid, true, (cudaStream_t)stream);
     if (rc) return rc;
     const size_t need = (size_t)grid * 4 * W * (size_t)c->edges;
     rc = ldpc::ensure_arena(const_cast<ldpc_code*>(c), need);
     if (rc) return rc;
     A.msg = reinterpret_cast<uint32_t*>(c->arena);
-    return dispatch(c, A, W, ctas_per_sm, &grid, false, (cudaStream_t)stream);
+    return dispatch(c, A, W, ctas_per_sm, threads, &grid, false, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ldpc_reconcile_persistent(const ldpc_code* code, const uint8_t* bob_bits, const int8_t* llr_mag,
+                              const int32_t* rank, const int32_t* n_short, const int32_t* n_punct,
+                              const uint8_t* known, const uint8_t* target_syndrome, int batch,
+                              const int32_t* frame_list, int list_len, int max_iter, int stall_window,
+                              int words, int ctas_per_sm, int threads, uint8_t* out_bits, int32_t* out_iters,
+                              uint8_t* out_ok, void* stream) {
+    return reconcile_common(code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome, batch,
+                            frame_list, list_len, max_iter, stall_window, nullptr, 0, words, ctas_per_sm, threads,
+                            out_bits, out_iters, out_ok, nullptr, stream);
+}
+
+int ldpc_reconcile_interactive(const ldpc_code* code, const uint8_t* bob_bits, const int8_t* llr_mag,
+                               const int32_t* rank, const int32_t* n_short, const int32_t* n_punct,
+                               const uint8_t* known, const uint8_t* target_syndrome, int batch,
+                               const int32_t* frame_list, int list_len, int max_iter, int stall_window,
+                               const int32_t* reveal, int max_rounds, int words, int ctas_per_sm, int threads,
+                               uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, int32_t* out_rounds,
+                               void* stream) {
+    using ldpc::fail;
+    if (!reveal || !out_rounds || max_rounds < 0)
+        return fail(LDPC_EINVAL, "interactive decode: needs the reveal table, out_rounds and max_rounds >= 0");
+    if (!rank || !n_short || !n_punct || !known)
+        return fail(LDPC_EINVAL, "interactive decode: needs the rank table, both counts and the known values");
+    return reconcile_common(code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome, batch,
+                            frame_list, list_len, max_iter, stall_window, reveal, max_rounds, words, ctas_per_sm,
+                            threads, out_bits, out_iters, out_ok, out_rounds, stream);
 }
 
 }  // extern "C"

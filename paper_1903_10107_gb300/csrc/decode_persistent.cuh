@@ -15,9 +15,13 @@
 //     puncturing and shortening only change the initial soft values of the
 //     shared mother code.  Per-frame results equal those of
 //     ldpc_decode_batch on the same soft values.
+//   * Interactive rounds (section 4.2) run inside the same launch: a frame
+//     that fails a round is rebuilt in its lane from the next round's reveal
+//     state (a per-frame table of revealed counts) and decoded again, so no
+//     round waits for the slowest frame of the previous one.
 #pragma once
 
-#include <math.h>
+#include <string>
 
 #include "decode_int8.cuh"
 
@@ -27,7 +31,7 @@ struct PersistArgs {
     const int32_t* tab;
     int Mb, nblk, Z, n, m;
     const uint8_t* bob;
-    const double* qber;
+    const int8_t* mag;  // per-frame channel LLR magnitude (host-computed)
     const int32_t* rank;
     const int32_t* n_short;
     const int32_t* n_punct;
@@ -35,10 +39,17 @@ struct PersistArgs {
     const uint8_t* syn;
     const int32_t* list;
     int batch, list_len, max_iter;
-    double scale;
+    int stall;  // stall window K (0 = off): a frame whose unsatisfied-check count set no new minimum
+                // in its last K iterations stops as a failure
     uint8_t* out_bits;
     int32_t* out_iters;
     uint8_t* out_ok;
+    // Interactive rounds (NULL reveal = one round): reveal[f][r] bits of frame f's puncturing order are
+    // revealed in round r (cumulative, reveal[f][0] = 0); a frame failing round r < max_rounds restarts
+    // in its lane from round r + 1's state.  out_rounds[f] = the last round decoded.
+    const int32_t* reveal;
+    int max_rounds;
+    int32_t* out_rounds;
     uint32_t* msg;
     int* queue;  // [0] frames claimed, [1] frames finished, [2..3] their iterations (64 bit); zeroed per launch
 };
@@ -68,9 +79,10 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
     int32_t* s_tab = reinterpret_cast<int32_t*>(smem + soft_bytes(n, W));
     uint8_t* syn_s = reinterpret_cast<uint8_t*>(s_tab + tab_words);
     constexpr int NL = 4 * W;
-    __shared__ int s_frame[NL], s_it[NL], s_mag[NL], s_ns[NL], s_np[NL];
+    __shared__ int s_frame[NL], s_it[NL], s_mag[NL], s_ns[NL], s_np[NL], s_ubest[NL], s_tbest[NL];
+    __shared__ int s_round[NL], s_itsum[NL];  // interactive round of the lane's frame, iterations of its earlier rounds
     __shared__ uint8_t s_done[NL], s_okf[NL];
-    __shared__ uint32_t s_active[W], s_fresh[W], s_bad[W], s_load[W];
+    __shared__ uint32_t s_active[W], s_fresh[W], s_bad[W], s_load[W], s_cnt[2 * W];
     __shared__ int s_base, s_any_load, s_any_done;
 
     const int tid = threadIdx.x, T = blockDim.x;
@@ -85,12 +97,16 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
         s_fresh[tid] = 0;
         s_bad[tid] = 0;
         s_load[tid] = 0;
+        s_cnt[2 * tid] = 0;
+        s_cnt[2 * tid + 1] = 0;
     }
     __syncthreads();
     if (tid < NL) {
         const int slot = s_base + tid;
         s_frame[tid] = frame_of(A, slot);
         s_done[tid] = 0;
+        s_round[tid] = 0;
+        s_itsum[tid] = 0;
     }
     __syncthreads();
     if (tid < W) {
@@ -119,12 +135,19 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
                 const int ww = tid >> 2, l = tid & 3;
                 if ((s_load[ww] >> (8 * l)) & 1u) {
                     const int f = s_frame[tid];
-                    const double qb = A.qber[f];
-                    long mag = lround(log((1.0 - qb) / qb) * A.scale);
-                    s_mag[tid] = (int)(mag > 127 ? 127 : (mag < -127 ? -127 : mag));
-                    s_ns[tid] = A.n_short ? A.n_short[f] : 0;
-                    s_np[tid] = A.n_punct ? A.n_punct[f] : 0;
+                    const int mg = A.mag[f];
+                    s_mag[tid] = mg > 127 ? 127 : (mg < -127 ? -127 : mg);
+                    int ns = A.n_short ? A.n_short[f] : 0, np = A.n_punct ? A.n_punct[f] : 0;
+                    if (A.reveal) {  // revealed positions: punctured ones first, all of them now shortened
+                        const int rv = A.reveal[(int64_t)f * (A.max_rounds + 1) + s_round[tid]];
+                        ns += rv;
+                        np = max(np - rv, 0);
+                    }
+                    s_ns[tid] = ns;
+                    s_np[tid] = np;
                     s_it[tid] = 0;
+                    s_ubest[tid] = 0x7FFFFFFF;
+                    s_tbest[tid] = 0;
                 }
             }
             __syncthreads();
@@ -207,11 +230,17 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
             __syncthreads();
         }
         uint32_t bad = 0;
+        uint32_t ulo = 0, uhi = 0;  // unsatisfied checks of lanes 0, 2 (ulo) and 1, 3 (uhi), 16 bits each
         {
             int i = q / Z, r = q - i * Z;
             const int di = QT / Z, dr = QT - di * Z;
             for (int c = q; c < m; c += QT) {
-                bad |= ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
+                const uint32_t p = ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
+                bad |= p;
+                if (A.stall) {
+                    ulo += (p >> 7) & 0x00010001u;
+                    uhi += (p >> 15) & 0x00010001u;
+                }
                 r += dr;
                 i += di;
                 if (r >= Z) {
@@ -223,6 +252,17 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
 #pragma unroll
         for (int o = 16; o >= W; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
         if ((tid & 31) < W && bad) atomicOr(&s_bad[w], bad);
+        if (A.stall) {
+#pragma unroll
+            for (int o = 16; o >= W; o >>= 1) {
+                ulo += __shfl_xor_sync(0xffffffffu, ulo, o);
+                uhi += __shfl_xor_sync(0xffffffffu, uhi, o);
+            }
+            if ((tid & 31) < W && (ulo | uhi)) {
+                atomicAdd(&s_cnt[2 * w], ulo);
+                atomicAdd(&s_cnt[2 * w + 1], uhi);
+            }
+        }
         if (tid == 0) s_any_done = 0;
         __syncthreads();
 
@@ -236,16 +276,36 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
                 const int lane = 4 * tid + l;
                 const int it = ++s_it[lane];
                 const bool ok = !(failing & lm);
-                if (ok || it >= A.max_iter) {
-                    s_done[lane] = 1;
-                    s_okf[lane] = ok ? 1 : 0;
+                bool stalled = false;
+                if (A.stall && !ok) {
+                    const int u = (int)((s_cnt[2 * tid + (l & 1)] >> (16 * (l >> 1))) & 0xFFFFu);
+                    if (u < s_ubest[lane]) {
+                        s_ubest[lane] = u;
+                        s_tbest[lane] = it;
+                    } else {
+                        stalled = it - s_tbest[lane] >= A.stall;
+                    }
+                }
+                if (ok || stalled || it >= A.max_iter) {
                     act &= ~lm;
-                    s_any_done = 1;
+                    if (!ok && A.reveal && s_round[lane] < A.max_rounds) {
+                        // the next interactive round: more bits revealed, decoded again in this lane
+                        s_itsum[lane] += it;
+                        ++s_round[lane];
+                        s_load[tid] |= lm;
+                        s_any_load = 1;
+                    } else {
+                        s_done[lane] = 1;
+                        s_okf[lane] = ok ? 1 : 0;
+                        s_any_done = 1;
+                    }
                 }
             }
             s_active[tid] = act;
             s_fresh[tid] = 0;
             s_bad[tid] = 0;
+            s_cnt[2 * tid] = 0;
+            s_cnt[2 * tid + 1] = 0;
         }
         __syncthreads();
         if (!s_any_done) continue;
@@ -274,8 +334,9 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
         }
         if (tid < NL && s_done[tid]) {
             const int64_t f = s_frame[tid];
-            A.out_iters[f] = s_it[tid];
+            A.out_iters[f] = s_itsum[tid] + s_it[tid];
             A.out_ok[f] = s_okf[tid];
+            if (A.out_rounds) A.out_rounds[f] = s_round[tid];
         }
         __syncthreads();
         // ---- claim the next frames for the finished and the idle lanes.  A
@@ -290,13 +351,16 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
             unsigned long long* done_iters = reinterpret_cast<unsigned long long*>(A.queue + 2);
             int fin = 0;
             unsigned long long fin_it = 0;
-            int oldest = 0;
+            int oldest = 0, oldest_end = A.max_iter;  // iterations of the oldest live frame, and when it ends at latest
             for (int lane = 0; lane < NL; ++lane) {
                 if (s_done[lane]) {
                     ++fin;
-                    fin_it += (unsigned)s_it[lane];
+                    fin_it += (unsigned)(s_itsum[lane] + s_it[lane]);
                 }
-                if ((s_active[lane >> 2] >> (8 * (lane & 3))) & 1u) oldest = max(oldest, s_it[lane]);
+                if (((s_active[lane >> 2] >> (8 * (lane & 3))) & 1u) && s_it[lane] > oldest) {
+                    oldest = s_it[lane];
+                    oldest_end = A.stall ? min(A.max_iter, s_tbest[lane] + A.stall) : A.max_iter;
+                }
             }
             const int done_f = atomicAdd(A.queue + 1, fin) + fin;
             const unsigned long long done_i = atomicAdd(done_iters, fin_it) + fin_it;
@@ -304,7 +368,7 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
             if (oldest >= kHoldAfter && done_f >= kHoldMinDone) {
                 const long long left = (long long)A.list_len - atomicAdd(A.queue, 0);
                 hold = left <= 0 || 3ull * (unsigned long long)left * done_i <
-                                        2ull * (unsigned long long)done_f * gridDim.x * NL * (A.max_iter - oldest);
+                                        2ull * (unsigned long long)done_f * gridDim.x * NL * (oldest_end - oldest);
             }
             int k = 0;
             for (int lane = 0; lane < NL; ++lane) k += (s_done[lane] || s_frame[lane] < 0) ? 1 : 0;
@@ -313,6 +377,8 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
             for (int lane = 0; lane < NL; ++lane) {
                 if (!s_done[lane] && s_frame[lane] >= 0) continue;  // still decoding
                 s_done[lane] = 0;
+                s_round[lane] = 0;
+                s_itsum[lane] = 0;
                 s_frame[lane] = hold ? -1 : frame_of(A, base + i++);
                 if (s_frame[lane] >= 0) {
                     s_load[lane >> 2] |= 0xFFu << (8 * (lane & 3));
@@ -325,12 +391,19 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
 
 
 template <int MAXH, int W>
-int launch_p(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int* grid_out, bool dry, cudaStream_t st) {
+int launch_p(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int threads, int* grid_out, bool dry,
+             cudaStream_t st) {
     constexpr int P = 2;
     constexpr int MAXT = max_threads<MAXH>();
     int T = c->Z * W * P;
     if (T > MAXT) T = MAXT;
     T = (T + 31) / 32 * 32;
+    if (threads > 0) {  // fewer threads than rows: each thread pair then takes several rows per layer
+        if (threads % (32 * W) || threads > MAXT)
+            return ldpc::fail(LDPC_EINVAL, "persistent decode: threads must be a multiple of 32*words and at most " +
+                                               std::to_string(MAXT));
+        T = threads;
+    }
     const size_t smem = smem_bytes(c, W);
     auto kern = persistent_kernel<MAXH, P, W, MAXT>;
     LDPC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -356,15 +429,16 @@ int launch_p(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int* gri
 // width MAXH with W words per row.  Instantiated once per width, each in its
 // own translation unit.
 template <int MAXH>
-int persist_launch(const ldpc_code* c, const PersistArgs& A, int W, int ctas_per_sm, int* grid, bool dry,
+int persist_launch(const ldpc_code* c, const PersistArgs& A, int W, int ctas_per_sm, int threads, int* grid, bool dry,
                    cudaStream_t st) {
-    if (W == 1) return launch_p<MAXH, 1>(c, A, ctas_per_sm, grid, dry, st);
-    if (W == 2) return launch_p<MAXH, 2>(c, A, ctas_per_sm, grid, dry, st);
-    return launch_p<MAXH, 4>(c, A, ctas_per_sm, grid, dry, st);
+    if (W == 1) return launch_p<MAXH, 1>(c, A, ctas_per_sm, threads, grid, dry, st);
+    if (W == 2) return launch_p<MAXH, 2>(c, A, ctas_per_sm, threads, grid, dry, st);
+    return launch_p<MAXH, 4>(c, A, ctas_per_sm, threads, grid, dry, st);
 }
 
 #define LDPC_PERSIST_EXTERN(M) \
-    extern template int persist_launch<M>(const ldpc_code*, const PersistArgs&, int, int, int*, bool, cudaStream_t);
+    extern template int persist_launch<M>(const ldpc_code*, const PersistArgs&, int, int, int, int*, bool, \
+                                          cudaStream_t);
 LDPC_MAXH_LIST(LDPC_PERSIST_EXTERN)
 #undef LDPC_PERSIST_EXTERN
 

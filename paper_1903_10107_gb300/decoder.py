@@ -27,6 +27,15 @@ def _dev_ptr(t: torch.Tensor | None, name: str, dtype, device, shape=None) -> in
     return t.data_ptr()
 
 
+def llr_magnitudes(qber, scale: float) -> np.ndarray:
+    """Per-frame channel-LLR magnitudes (section 3.1), ``int8[B]``, computed
+    on the host by the library (``ldpc_llr_magnitudes``) from host QBERs."""
+    q = np.ascontiguousarray(np.atleast_1d(np.asarray(qber, dtype=np.float64)))
+    out = np.empty(q.size, dtype=np.int8)
+    native.ldpc_llr_magnitudes(q.ctypes.data, int(q.size), float(scale), out.ctypes.data)
+    return out
+
+
 class QCCode:
     """A quasi-cyclic LDPC code (section 4.1) resident on one GPU.
 
@@ -77,13 +86,14 @@ class QCCode:
         native.ldpc_syndrome(self.handle, bits.data_ptr(), B, out.data_ptr(), self._stream())
         return out
 
-    def llr_from_bsc(self, bob_bits, qber, rank=None, n_short=None, n_punct=None, known=None, scale: float = 8.0,
+    def llr_from_bsc(self, bob_bits, llr_mag, rank=None, n_short=None, n_punct=None, known=None,
                      out=None) -> torch.Tensor:
         """Quantised channel LLRs ``int8[B][n]`` (section 3.1) with punctured and
-        shortened positions (section 4.1)."""
+        shortened positions (section 4.1); ``llr_mag`` is the device copy of
+        ``llr_magnitudes(qber, scale)``."""
         B = bob_bits.shape[0]
         _dev_ptr(bob_bits, "bob_bits", torch.uint8, self.device, (B, self.nbytes))
-        _dev_ptr(qber, "qber", torch.float64, self.device, (B,))
+        _dev_ptr(llr_mag, "llr_mag", torch.int8, self.device, (B,))
         rp = _dev_ptr(rank, "rank", torch.int32, self.device, (self.n,))
         sp = _dev_ptr(n_short, "n_short", torch.int32, self.device, (B,))
         pp = _dev_ptr(n_punct, "n_punct", torch.int32, self.device, (B,))
@@ -91,7 +101,7 @@ class QCCode:
         if out is None:
             out = torch.empty((B, self.n), dtype=torch.int8, device=self.device)
         _dev_ptr(out, "out", torch.int8, self.device, (B, self.n))
-        native.ldpc_llr_from_bsc(self.handle, bob_bits.data_ptr(), qber.data_ptr(), rp, sp, pp, kp, B, float(scale),
+        native.ldpc_llr_from_bsc(self.handle, bob_bits.data_ptr(), llr_mag.data_ptr(), rp, sp, pp, kp, B,
                                  out.data_ptr(), self._stream())
         return out
 
@@ -128,19 +138,19 @@ class QCCode:
         return bits, iters, ok
 
 
-    def reserve_persistent(self, list_len: int, words: int = 0, ctas_per_sm: int = 0) -> None:
+    def reserve_persistent(self, list_len: int, words: int = 0, ctas_per_sm: int = 0, threads: int = 0) -> None:
         with torch.cuda.device(self.device):
-            native.ldpc_code_reserve_persistent(self.handle, int(list_len), int(words), int(ctas_per_sm))
+            native.ldpc_code_reserve_persistent(self.handle, int(list_len), int(words), int(ctas_per_sm), int(threads))
 
-    def reconcile_persistent(self, bob_bits, qber, syndrome, max_iter: int, rank=None, n_short=None, n_punct=None,
-                             known=None, frame_list=None, llr_scale: float = 8.0, words: int = 0,
-                             ctas_per_sm: int = 0, out=None):
+    def reconcile_persistent(self, bob_bits, llr_mag, syndrome, max_iter: int, rank=None, n_short=None, n_punct=None,
+                             known=None, frame_list=None, stall_window: int = 0, words: int = 0,
+                             ctas_per_sm: int = 0, threads: int = 0, out=None):
         """Fused LLR quantisation + layered decoding in one persistent launch
         (frames indexed by id; ``frame_list`` selects which to decode).
         Returns ``(bits, iters, ok)`` indexed by frame id."""
         B = bob_bits.shape[0]
         _dev_ptr(bob_bits, "bob_bits", torch.uint8, self.device, (B, self.nbytes))
-        _dev_ptr(qber, "qber", torch.float64, self.device, (B,))
+        _dev_ptr(llr_mag, "llr_mag", torch.int8, self.device, (B,))
         _dev_ptr(syndrome, "syndrome", torch.uint8, self.device, (B, self.mbytes))
         rp = _dev_ptr(rank, "rank", torch.int32, self.device, (self.n,))
         sp = _dev_ptr(n_short, "n_short", torch.int32, self.device, (B,))
@@ -160,11 +170,54 @@ class QCCode:
         _dev_ptr(iters, "out iters", torch.int32, self.device, (B,))
         _dev_ptr(ok, "out ok", torch.uint8, self.device, (B,))
         with torch.cuda.device(self.device):
-            native.ldpc_reconcile_persistent(self.handle, bob_bits.data_ptr(), qber.data_ptr(), rp, sp, pp, kp,
-                                             syndrome.data_ptr(), B, lp, nl, int(max_iter), float(llr_scale),
-                                             int(words), int(ctas_per_sm), bits.data_ptr(), iters.data_ptr(),
-                                             ok.data_ptr(), self._stream())
+            native.ldpc_reconcile_persistent(self.handle, bob_bits.data_ptr(), llr_mag.data_ptr(), rp, sp, pp, kp,
+                                             syndrome.data_ptr(), B, lp, nl, int(max_iter), int(stall_window),
+                                             int(words), int(ctas_per_sm), int(threads), bits.data_ptr(),
+                                             iters.data_ptr(), ok.data_ptr(), self._stream())
         return bits, iters, ok
+
+
+    def reconcile_interactive(self, bob_bits, llr_mag, syndrome, max_iter: int, rank, n_short, n_punct, known,
+                              reveal, frame_list=None, stall_window: int = 0, words: int = 0, ctas_per_sm: int = 0,
+                              threads: int = 0, out=None):
+        """All interactive rounds in one persistent launch
+        (``ldpc_reconcile_interactive``): ``n_short``/``n_punct`` are round
+        0's counts, ``reveal`` ``int32[B][max_rounds + 1]`` the cumulative
+        revealed bits per round.  Returns ``(bits, iters, ok, rounds)``
+        indexed by frame id (iterations summed over rounds)."""
+        B = bob_bits.shape[0]
+        R = int(reveal.shape[1]) - 1
+        _dev_ptr(bob_bits, "bob_bits", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(llr_mag, "llr_mag", torch.int8, self.device, (B,))
+        _dev_ptr(syndrome, "syndrome", torch.uint8, self.device, (B, self.mbytes))
+        _dev_ptr(rank, "rank", torch.int32, self.device, (self.n,))
+        _dev_ptr(n_short, "n_short", torch.int32, self.device, (B,))
+        _dev_ptr(n_punct, "n_punct", torch.int32, self.device, (B,))
+        _dev_ptr(known, "known", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(reveal, "reveal", torch.int32, self.device, (B, R + 1))
+        if frame_list is not None:
+            lp = _dev_ptr(frame_list, "frame_list", torch.int32, self.device)
+            nl = int(frame_list.numel())
+        else:
+            lp, nl = None, B
+        if out is None:
+            out = (torch.zeros((B, self.nbytes), dtype=torch.uint8, device=self.device),
+                   torch.zeros((B,), dtype=torch.int32, device=self.device),
+                   torch.zeros((B,), dtype=torch.uint8, device=self.device),
+                   torch.zeros((B,), dtype=torch.int32, device=self.device))
+        bits, iters, ok, rounds = out
+        _dev_ptr(bits, "out bits", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(iters, "out iters", torch.int32, self.device, (B,))
+        _dev_ptr(ok, "out ok", torch.uint8, self.device, (B,))
+        _dev_ptr(rounds, "out rounds", torch.int32, self.device, (B,))
+        with torch.cuda.device(self.device):
+            native.ldpc_reconcile_interactive(self.handle, bob_bits.data_ptr(), llr_mag.data_ptr(), rank.data_ptr(),
+                                              n_short.data_ptr(), n_punct.data_ptr(), known.data_ptr(),
+                                              syndrome.data_ptr(), B, lp, nl, int(max_iter), int(stall_window),
+                                              reveal.data_ptr(), R, int(words), int(ctas_per_sm), int(threads),
+                                              bits.data_ptr(), iters.data_ptr(), ok.data_ptr(), rounds.data_ptr(),
+                                              self._stream())
+        return bits, iters, ok, rounds
 
 
 def tau_table_device(device=None) -> torch.Tensor:

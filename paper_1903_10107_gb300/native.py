@@ -35,13 +35,17 @@ SIGNATURES = {
     "ldpc_code_destroy": (None, [_P]),
     "ldpc_code_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64), ctypes.POINTER(_I)]),
     "ldpc_code_reserve": (_I, [_P, _I]),
-    "ldpc_llr_from_bsc": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _D, _P, _P]),
+    "ldpc_llr_magnitudes": (_I, [_P, _I, _D, _P]),
+    "ldpc_llr_from_bsc": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _P, _P]),
     "ldpc_syndrome": (_I, [_P, _P, _I, _P, _P]),
     "ldpc_decode_batch": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "ldpc_decode_batch_ex": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P, _P]),
     "ldpc_decode_batch_words": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P]),
-    "ldpc_reconcile_persistent": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _D, _I, _I, _P, _P, _P, _P]),
-    "ldpc_code_reserve_persistent": (_I, [_P, _I, _I, _I]),
+    "ldpc_reconcile_persistent": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P,
+                                       _P]),
+    "ldpc_reconcile_interactive": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _I, _I, _I, _I, _P,
+                                        _P, _P, _P, _P]),
+    "ldpc_code_reserve_persistent": (_I, [_P, _I, _I, _I, _I]),
     "ldpc_relaxed_forward": (_I, [_P, _P, _P, _P, _I, _I, _P, _P, _P, _I, ctypes.c_float, _P, _P, _P, _P]),
     "ldpc_relaxed_backward": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P,
                                    _P]),
@@ -114,8 +118,12 @@ def ldpc_code_reserve(code: int, batch: int) -> None:
     _call("ldpc_code_reserve", code, batch)
 
 
-def ldpc_llr_from_bsc(code, bob_bits, qber, rank, n_short, n_punct, known, batch, scale, llr_out, stream):
-    _call("ldpc_llr_from_bsc", code, bob_bits, qber, rank, n_short, n_punct, known, batch, scale, llr_out, stream)
+def ldpc_llr_magnitudes(qber, batch, scale, mag_out):
+    _call("ldpc_llr_magnitudes", qber, batch, scale, mag_out)
+
+
+def ldpc_llr_from_bsc(code, bob_bits, llr_mag, rank, n_short, n_punct, known, batch, llr_out, stream):
+    _call("ldpc_llr_from_bsc", code, bob_bits, llr_mag, rank, n_short, n_punct, known, batch, llr_out, stream)
 
 
 def ldpc_syndrome(code, bits, batch, syn_out, stream):
@@ -138,15 +146,24 @@ def ldpc_decode_batch_words(code, llr_in, target_syndrome, batch, max_iter, word
           out_ok, stream)
 
 
-def ldpc_reconcile_persistent(code, bob_bits, qber, rank, n_short, n_punct, known, target_syndrome, batch,
-                              frame_list, list_len, max_iter, llr_scale, words, ctas_per_sm, out_bits, out_iters,
-                              out_ok, stream):
-    _call("ldpc_reconcile_persistent", code, bob_bits, qber, rank, n_short, n_punct, known, target_syndrome, batch,
-          frame_list, list_len, max_iter, llr_scale, words, ctas_per_sm, out_bits, out_iters, out_ok, stream)
+def ldpc_reconcile_persistent(code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome, batch,
+                              frame_list, list_len, max_iter, stall_window, words, ctas_per_sm, threads, out_bits,
+                              out_iters, out_ok, stream):
+    _call("ldpc_reconcile_persistent", code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome,
+          batch, frame_list, list_len, max_iter, stall_window, words, ctas_per_sm, threads, out_bits, out_iters,
+          out_ok, stream)
 
 
-def ldpc_code_reserve_persistent(code, list_len, words, ctas_per_sm):
-    _call("ldpc_code_reserve_persistent", code, list_len, words, ctas_per_sm)
+def ldpc_reconcile_interactive(code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome, batch,
+                               frame_list, list_len, max_iter, stall_window, reveal, max_rounds, words, ctas_per_sm,
+                               threads, out_bits, out_iters, out_ok, out_rounds, stream):
+    _call("ldpc_reconcile_interactive", code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome,
+          batch, frame_list, list_len, max_iter, stall_window, reveal, max_rounds, words, ctas_per_sm, threads,
+          out_bits, out_iters, out_ok, out_rounds, stream)
+
+
+def ldpc_code_reserve_persistent(code, list_len, words, ctas_per_sm, threads=0):
+    _call("ldpc_code_reserve_persistent", code, list_len, words, ctas_per_sm, threads)
 
 
 def ldpc_relaxed_forward(code, llr, syn, bits, batch, iters, alpha, gamma, layer_class, n_classes, kappa, ckE, ckL,

@@ -33,7 +33,7 @@ import numpy as np
 import torch
 
 from . import inputs, rate
-from .decoder import QCCode
+from .decoder import QCCode, llr_magnitudes
 from .pipeline import hardest_first
 
 
@@ -125,14 +125,14 @@ class ReconciliationServer:
             d_obs = pin(obs).to(dev, non_blocking=True)
             d_other = pin(truth_other).to(dev, non_blocking=True)  # the other party's key, for its syndrome
             d_known = pin(known).to(dev, non_blocking=True)
-            d_q = pin(q).to(dev, non_blocking=True)
+            d_mag = pin(llr_magnitudes(q, self.llr_scale)).to(dev, non_blocking=True)
             d_np = pin(npn).to(dev, non_blocking=True)
             d_ns = pin(nsh).to(dev, non_blocking=True)
             order = torch.from_numpy(hardest_first(npn, nsh, q)).pin_memory().to(dev, non_blocking=True)
             syn = slot.code.syndrome(d_other)  # the syndrome each side receives from the other
-            bits, iters, ok = slot.code.reconcile_persistent(d_obs, d_q, syn, self.max_iter, rank=e.rank, n_short=d_ns,
-                                                             n_punct=d_np, known=d_known, frame_list=order,
-                                                             llr_scale=self.llr_scale)
+            bits, iters, ok = slot.code.reconcile_persistent(d_obs, d_mag, syn, self.max_iter, rank=e.rank,
+                                                             n_short=d_ns, n_punct=d_np, known=d_known,
+                                                             frame_list=order)
             h_bits = torch.empty(bits.shape, dtype=torch.uint8, pin_memory=True)
             h_iters = torch.empty(iters.shape, dtype=torch.int32, pin_memory=True)
             h_ok = torch.empty(ok.shape, dtype=torch.uint8, pin_memory=True)
@@ -142,7 +142,7 @@ class ReconciliationServer:
             ev = torch.cuda.Event()
             ev.record(slot.stream)
             # keep device tensors alive until the launch completes
-            slot.keep = (d_obs, d_other, d_known, d_q, d_np, d_ns, order, syn, bits, iters, ok)
+            slot.keep = (d_obs, d_other, d_known, d_mag, d_np, d_ns, order, syn, bits, iters, ok)
         slot.busy, slot.event, slot.host_out = list(reqs), ev, (h_bits, h_iters, h_ok, truth_other)
         slot.nbytes_held = self._need(e, k)
         self.held += slot.nbytes_held

@@ -22,7 +22,7 @@ import numpy as np
 import torch
 
 from . import inputs
-from .decoder import QCCode
+from .decoder import QCCode, llr_magnitudes
 from .relaxed import RelaxedDecoder, bsc_llr_nats, kappa_for_scale
 
 
@@ -79,7 +79,7 @@ def main(argv=None):
     xa, yb, q = frames(w, args.eval_frames, 10_000, qlo, qhi)
     d_xa = c(xa)
     syn = code.syndrome(d_xa)
-    llr_q = code.llr_from_bsc(c(yb), c(q), scale=args.llr_scale)
+    llr_q = code.llr_from_bsc(c(yb), c(llr_magnitudes(q, args.llr_scale)))
     res = {}
     for name, tabs in (("untuned", (None, None)), ("learned", (c(sq), c(oq)))):
         bits, iters, ok = code.decode(llr_q, syn, w.max_iter, scale_q4=tabs[0], offset_q=tabs[1])

@@ -22,3 +22,12 @@ def golden(name):
             if line:
                 rows.append(line.split())
     return rows
+
+
+def device_mags(q, scale=8.0):
+    """Per-frame int8 LLR magnitudes of host QBERs (the library's host
+    function), as a CUDA tensor: the decoders' per-frame input."""
+    import numpy as np
+    import torch
+    from paper_1903_10107_gb300.decoder import llr_magnitudes
+    return torch.from_numpy(llr_magnitudes(np.asarray(q, dtype=np.float64), scale)).cuda()

@@ -40,26 +40,39 @@ def test_kernel_sha_ignores_comments_and_layout_only(fake_root):
 def test_profiled_bytes_only_for_the_current_kernels(fake_root):
     sha = bench.kernel_sources_sha()
     p = fake_root / "profiles" / "persistent_kernel_wl.md"
-    p.write_text(f"# title\n\nkernel_sha: {sha}\ndram_bytes_per_frame: 1000.5\nl2_bytes_per_frame: 2500\n")
-    assert bench.profiled_traffic("persistent_kernel", "wl", 4) == pytest.approx(4002.0)
-    assert bench.profiled_traffic("persistent_kernel", "wl", 4, "l2_bytes_per_frame") == pytest.approx(10000.0)
-    assert bench.profiled_traffic("decode_kernel", "wl", 4) is None  # no summary
-    p.write_text("kernel_sha: 0123456789abcdef\ndram_bytes_per_frame: 1000.5\n")
-    assert bench.profiled_traffic("persistent_kernel", "wl", 4) is None  # stale summary
+    p.write_text(f"# title\n\nkernel_sha: {sha}\ndram_bytes_per_frame_iteration: 1000.5\n"
+                 "l2_bytes_per_frame_iteration: 2500\n")
+    assert bench.profile_value("persistent_kernel", "wl", "dram_bytes_per_frame_iteration") == pytest.approx(1000.5)
+    assert bench.profile_value("persistent_kernel", "wl", "l2_bytes_per_frame_iteration") == pytest.approx(2500.0)
+    assert bench.profile_value("decode_kernel", "wl", "dram_bytes_per_frame_iteration") is None  # no summary
+    p.write_text("kernel_sha: 0123456789abcdef\ndram_bytes_per_frame_iteration: 1000.5\n")
+    assert bench.profile_value("persistent_kernel", "wl", "dram_bytes_per_frame_iteration") is None  # stale
 
 
 def test_committed_profiles_parse():
-    for kernel, wl in (("persistent_kernel", "n49152_mixed_q01_08"), ("decode_kernel", "n40960_r080_q03")):
-        path = os.path.join(bench.ROOT, "profiles", f"{kernel}_{wl}.md")
+    import glob
+    paths = [p for p in glob.glob(os.path.join(bench.ROOT, "profiles", "*.md")) if "kernel_sha:" in open(p).read()]
+    assert paths
+    for path in paths:
         txt = open(path).read()
-        assert "kernel_sha:" in txt and "dram_bytes_per_frame:" in txt and "l2_bytes_per_frame:" in txt
-        assert "--clock-control none" in txt
+        assert "dram_bytes_per_frame_iteration:" in txt and "--clock-control none" in txt, path
 
 
-def test_roofline_alu_arithmetic(monkeypatch):
-    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
-    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda i: types.SimpleNamespace(multi_processor_count=152))
-    r = bench.roofline_alu(it_sum=1000, edges=192000, seconds=0.01, clk={"sm_mhz": 2000.0})
+def test_workload_config_is_the_same_for_both_arms():
+    args = bench.parse_args([])
+    w = bench.inputs.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    a = bench.workload_config(args, w, 16384, 1)
+    assert a == bench.workload_config(bench.parse_args(["--impl", "reference"]), w, 16384, 1)
+    assert a["protocol"].startswith("interactive") and a["f_start"] == 1.1 and a["max_iter"] == 200
+    assert "no flush" in a["l2"]
+    f = bench.workload_config(bench.parse_args(["--protocol", "fixed"]), w, 16384, 1)
+    assert f["target_f"] == w.target_f and "f_start" not in f
+    small = bench.workload_config(args, bench.inputs.WORKLOADS["n4096_r075_q02"], 64, 1)
+    assert small["l2"].startswith("L2 flushed") and small["protocol"].startswith("single code")
+
+
+def test_roofline_alu_arithmetic():
+    r = bench.roofline_alu(it_sum=1000, edges=192000, seconds=0.01, clk={"sm_mhz": 2000.0}, sms=152)
     assert r["peak"] == pytest.approx(152 * 4 * 32 * 2000e6 * 4 / 1e12)
     assert r["achieved"] == pytest.approx(bench.ALU_OPS_PER_EDGE * 192000 * 1000 / 0.01 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
@@ -67,10 +80,17 @@ def test_roofline_alu_arithmetic(monkeypatch):
     assert bench.roofline_alu(1, 1, 1.0, None)["peak"] == pytest.approx(152 * 4 * 32 * 2070e6 * 4 / 1e12)
 
 
+def test_roofline_hbm_arithmetic(fake_root):
+    (fake_root / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6000.0}')
+    r = bench.roofline_hbm(3e9, 0.001, "persistent_kernel", None)
+    assert r["achieved"] == pytest.approx(3000.0) and r["frac"] == pytest.approx(0.5)
+    assert r["peak_kind"].startswith("measured") and r["bound"] == "hbm" and r["unit"] == "GB/s"
+
+
 def test_peak_source(fake_root):
     assert bench.peaks() == (6800.0, "fallback")
     (fake_root / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6691.8}')
-    assert bench.peaks() == (6691.8, "measured")
+    assert bench.peaks()[0] == 6691.8 and bench.peaks()[1].startswith("measured")
 
 
 def test_clock_samples_median_and_reasons(monkeypatch):

@@ -15,6 +15,7 @@ ok => H x = s, not ok => iterations = max_iter, 1 <= iterations <= max_iter.
 import numpy as np
 import pytest
 
+from conftest import device_mags
 from oracle import core as orc
 from oracle import rate as orate
 from paper_1903_10107_gb300 import inputs
@@ -67,7 +68,7 @@ def test_mixed_rate_full_size_sampled_frames_match_oracle():
 
     rec = Reconciler(base, w.Z, tb, llr_scale=w.llr_scale)
     syn = rec.code.syndrome(_dev(xa))
-    mrb = MixedRateBatch(rec, w.max_iter).bind(_dev(yb), syn, _dev(q), _dev(npn), _dev(ns), _dev(xa),
+    mrb = MixedRateBatch(rec, w.max_iter).bind(_dev(yb), syn, _dev(rec.magnitudes(q)), _dev(npn), _dev(ns), _dev(xa),
                                                order=hardest_first(npn, ns, q))
     assert mrb.graph is not None
     for t in mrb.out:
@@ -97,7 +98,7 @@ def test_n40960_full_batch_sampled_frames_match_oracle():
     xa, yb, q = w.frames(B, 0)
     code = QCCode(base, w.Z)
     d_syn = code.syndrome(_dev(xa))
-    llr = code.llr_from_bsc(_dev(yb), _dev(q), scale=w.llr_scale)
+    llr = code.llr_from_bsc(_dev(yb), device_mags(q, w.llr_scale))
     bits, iters, ok = code.decode(llr, d_syn, w.max_iter)
     bits, iters, ok = bits.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy()
 
@@ -111,3 +112,46 @@ def test_n40960_full_batch_sampled_frames_match_oracle():
     ob, oi, oo, _ = orc.decode(base, w.Z, o_llr, syn_u[sel], w.max_iter)
     assert np.array_equal(oi, iters[sel]) and np.array_equal(oo, ok[sel])
     assert np.array_equal(ob, inputs.unpack_bits(bits[sel], w.n))
+
+
+def test_interactive_protocol_full_size_sampled_frames_match_oracle():
+    """The benchmark's default step at full size: the interactive protocol
+    from f = 1.1 over all 16384 frames of the n = 49152 mixed workload, every
+    round in one autotuned persistent launch with the benchmark's stall
+    window.  Sampled frames (seeded picks, failing frames, the longest) run
+    the oracle's protocol one by one and must agree in every field; every
+    frame satisfies ok => H x = s, not ok => H x != s after the last round."""
+    import bench
+    from oracle import protocol as oproto
+    from paper_1903_10107_gb300.pipeline import InteractiveProtocol, Reconciler
+
+    args = bench.parse_args([])
+    w = inputs.WORKLOADS[args.workload]
+    B = w.batch
+    base = w.base()
+    xa, yb, q = w.frames(B, 0)
+    tb = inputs.tiebreak_permutation(w.n, w.code_seed)
+    rec = Reconciler(base, w.Z, tb, llr_scale=w.llr_scale)
+    syn = rec.code.syndrome(_dev(xa))
+    proto = InteractiveProtocol(rec, w.max_iter, f_start=args.f_start, df=args.df, max_rounds=args.max_rounds,
+                                stall_window=args.stall_window)
+    proto.tune(_dev(yb), syn, q, _dev(xa))
+    res = proto.run(_dev(yb), syn, q, _dev(xa))
+    bits, iters, ok, rounds = res["bits"], res["iters"], res["ok"], res["rounds"]
+
+    syn_u = _syndromes(base, w.Z, w.n, xa)
+    R = args.max_rounds
+    assert np.all(rounds[ok == 0] == R) and rounds.max() <= R
+    assert np.all(iters >= rounds + 1) and np.all(iters <= (rounds + 1) * w.max_iter)
+    for f0 in range(0, B, 2048):
+        sl = slice(f0, f0 + 2048)
+        match = np.all(orc.syndrome(base, w.Z, inputs.unpack_bits(bits[sl], w.n)) == syn_u[sl], axis=1)
+        assert np.all(match[ok[sl] == 1]) and not np.any(match[ok[sl] == 0])
+
+    sel = _sample(iters, ok, B, seed=13, n_rand=10, n_fail=2, n_long=2)
+    ref = oproto.interactive(base, w.Z, tb, inputs.unpack_bits(xa[sel], w.n), inputs.unpack_bits(yb[sel], w.n),
+                             q[sel], args.f_start, args.df, R, w.max_iter, w.llr_scale,
+                             stall_window=args.stall_window)
+    assert np.array_equal(inputs.unpack_bits(bits[sel], w.n), ref["bits"])
+    for k in ("ok", "iters", "rounds", "revealed", "key_bits"):
+        assert np.array_equal(np.asarray(res[k])[sel], np.asarray(ref[k])), k

@@ -7,6 +7,7 @@ C ABI (via the thin ctypes binding)."""
 import numpy as np
 import pytest
 
+from conftest import device_mags
 from oracle import core as orc
 from oracle import rate as orate
 from paper_1903_10107_gb300 import inputs
@@ -90,8 +91,14 @@ def test_llr_kernel_plain_and_rate_adapted():
     B = 40
     q = inputs.frame_qbers(B, 0.01, 0.08, 3)
     q[:4] = [0.01, 0.02, 0.03, 0.08]
+    # QBERs whose ln((1-q)/q) * 8 lies within 1e-12 of a half-integer (k + 1/2, k = 20..35)
+    import math
+    for i, k in enumerate(range(20, 36)):
+        q0 = 1.0 / (1.0 + math.exp((k + 0.5) / 8.0))
+        q[4 + i] = math.nextafter(q0, 1.0) if i % 2 else q0
+        assert abs(math.log((1 - q[4 + i]) / q[4 + i]) * 8.0 - (k + 0.5)) < 1e-12
     xa, yb = _frames(base, Z, B, q, 11)
-    got = code.llr_from_bsc(_cuda(yb), _cuda(q)).cpu().numpy()
+    got = code.llr_from_bsc(_cuda(yb), device_mags(q)).cpu().numpy()
     want = orc.llr_frames(inputs.unpack_bits(yb, n), q)
     assert np.array_equal(got, want)
     # rate adapted: rank, shortened and punctured counts
@@ -100,7 +107,7 @@ def test_llr_kernel_plain_and_rate_adapted():
     ns = np.array([orate.rate_plan(n, m, float(x), 1.1)[1] for x in q], dtype=np.int32)
     npn = np.array([orate.rate_plan(n, m, float(x), 1.1)[0] for x in q], dtype=np.int32)
     ns[5] += 7  # a frame with both kinds, as after an interactive reveal
-    got = code.llr_from_bsc(_cuda(yb), _cuda(q), rank=_cuda(rank), n_short=_cuda(ns), n_punct=_cuda(npn),
+    got = code.llr_from_bsc(_cuda(yb), device_mags(q), rank=_cuda(rank), n_short=_cuda(ns), n_punct=_cuda(npn),
                             known=_cuda(xa)).cpu().numpy()
     st = np.stack([orate.position_states(rank, int(npn[f]), int(ns[f])) for f in range(B)])
     want = orc.llr_frames(inputs.unpack_bits(yb, n), q, st, inputs.unpack_bits(xa, n))
@@ -245,7 +252,7 @@ def test_every_unroll_width_batch_and_persistent(dmax):
     _assert_same(gg, o)
     code = QCCode(base, Z)
     qv = np.full(B, q)
-    bits, iters, ok = code.reconcile_persistent(_cuda(yb), _cuda(qv), _cuda(inputs.pack_bits(syn_u)), T)
+    bits, iters, ok = code.reconcile_persistent(_cuda(yb), device_mags(qv), _cuda(inputs.pack_bits(syn_u)), T)
     torch.cuda.synchronize()
     _assert_same((inputs.unpack_bits(bits.cpu().numpy(), code.n), iters.cpu().numpy(), ok.cpu().numpy()), o)
 

@@ -3,6 +3,7 @@ decoding with lane refill) with the CPU oracle, and its CUDA-graph capture."""
 import numpy as np
 import pytest
 
+from conftest import device_mags
 from oracle import core as orc
 from oracle import rate as orate
 from paper_1903_10107_gb300 import inputs
@@ -32,7 +33,7 @@ def _mixed_case(B, Z=32, seed=3, f_target=1.5, scale=8.0, Mb=24, Nb=96):
                 scale=scale)
 
 
-def _run(case, max_iter, words=0, ctas=0, frame_list=None):
+def _run(case, max_iter, words=0, ctas=0, frame_list=None, threads=0, stall=0):
     from paper_1903_10107_gb300.decoder import QCCode
     code = QCCode(case["base"], case["Z"])
     c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -41,11 +42,11 @@ def _run(case, max_iter, words=0, ctas=0, frame_list=None):
                 torch.full((B,), -7, dtype=torch.int32, device="cuda"),
                 torch.full((B,), 9, dtype=torch.uint8, device="cuda"))
     fl = None if frame_list is None else c(np.asarray(frame_list, dtype=np.int32))
-    bits, iters, ok = code.reconcile_persistent(c(case["yb"]), c(case["q"]), c(inputs.pack_bits(case["syn_u"])),
-                                                max_iter, rank=c(case["rank"]), n_short=c(case["ns"]),
-                                                n_punct=c(case["npn"]), known=c(case["xa"]), frame_list=fl,
-                                                llr_scale=case["scale"], words=words, ctas_per_sm=ctas,
-                                                out=sentinel)
+    bits, iters, ok = code.reconcile_persistent(c(case["yb"]), device_mags(case["q"], case["scale"]),
+                                                c(inputs.pack_bits(case["syn_u"])), max_iter, rank=c(case["rank"]),
+                                                n_short=c(case["ns"]), n_punct=c(case["npn"]), known=c(case["xa"]),
+                                                frame_list=fl, stall_window=stall, words=words, ctas_per_sm=ctas,
+                                                threads=threads, out=sentinel)
     torch.cuda.synchronize()
     return code, bits.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy()
 
@@ -90,7 +91,7 @@ def test_persistent_plain_inputs_without_rate_adaptation():
     c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     n = w.n
     syn_u = orc.syndrome(base, w.Z, inputs.unpack_bits(xa, n))
-    bits, iters, ok = code.reconcile_persistent(c(yb), c(q), c(inputs.pack_bits(syn_u)), w.max_iter)
+    bits, iters, ok = code.reconcile_persistent(c(yb), device_mags(q), c(inputs.pack_bits(syn_u)), w.max_iter)
     ob, oi, oo, _ = orc.decode(base, w.Z, orc.llr_frames(inputs.unpack_bits(yb, n), q), syn_u, w.max_iter)
     assert np.array_equal(inputs.unpack_bits(bits.cpu().numpy(), n), ob)
     assert np.array_equal(iters.cpu().numpy(), oi) and np.array_equal(ok.cpu().numpy(), oo)
@@ -101,9 +102,8 @@ def test_persistent_launch_captured_in_cuda_graph():
     from paper_1903_10107_gb300.decoder import QCCode
     code = QCCode(case["base"], case["Z"])
     c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    args = (c(case["yb"]), c(case["q"]), c(inputs.pack_bits(case["syn_u"])), 30)
-    kw = dict(rank=c(case["rank"]), n_short=c(case["ns"]), n_punct=c(case["npn"]), known=c(case["xa"]),
-              llr_scale=case["scale"])
+    args = (c(case["yb"]), device_mags(case["q"], case["scale"]), c(inputs.pack_bits(case["syn_u"])), 30)
+    kw = dict(rank=c(case["rank"]), n_short=c(case["ns"]), n_punct=c(case["npn"]), known=c(case["xa"]))
     B = len(case["q"])
     out = (torch.zeros((B, code.nbytes), dtype=torch.uint8, device="cuda"),
            torch.zeros((B,), dtype=torch.int32, device="cuda"),
@@ -141,3 +141,73 @@ def test_persistent_sizes_not_multiples_of_eight(Z, Mb, Nb):
     # padding bits past n in the last output byte stay 0
     pad = 8 * bits.shape[1] - case["n"]
     assert np.all(bits[:, -1] >> (8 - pad) == 0)
+
+
+@pytest.mark.parametrize("words", [1, 2, 4])
+@pytest.mark.parametrize("stall", [2, 6])
+def test_persistent_stall_window_bit_exact(words, stall):
+    """The stall rule (a frame whose count of unsatisfied checks sets no new
+    minimum for K iterations stops as a failure): per-lane counts in the
+    kernel against the oracle's, through bits, iteration counts and flags.
+    A high-QBER, low-efficiency case so that frames stall."""
+    case = _mixed_case(61, seed=31, f_target=1.25, scale=1 / 0.29)
+    code, bits, iters, ok = _run(case, 60, words=words, stall=stall)
+    ob, oi, oo, _ = orc.decode(case["base"], case["Z"], case["llr"], case["syn_u"], 60, stall_window=stall)
+    assert np.array_equal(ok, oo) and np.array_equal(iters, oi)
+    assert np.array_equal(inputs.unpack_bits(bits, case["n"]), ob)
+    stalled = (oo == 0) & (oi < 60)
+    assert stalled.any() and oo.any()  # frames stopped by the rule, and frames that decoded
+
+
+def test_persistent_fewer_threads_than_rows():
+    """threads below one pair per row of a layer: every thread pair takes
+    several rows per layer; results do not change."""
+    case = _mixed_case(29, Z=64, seed=17, f_target=1.5)
+    _, b1, i1, o1 = _run(case, 30)
+    for threads in (64, 32 * 3):
+        _, b2, i2, o2 = _run(case, 30, threads=threads)
+        assert np.array_equal(b1, b2) and np.array_equal(i1, i2) and np.array_equal(o1, o2)
+    ob, oi, oo, _ = orc.decode(case["base"], case["Z"], case["llr"], case["syn_u"], 30)
+    assert np.array_equal(o1, oo) and np.array_equal(i1, oi)
+
+
+def test_persistent_rejects_bad_thread_counts():
+    from paper_1903_10107_gb300 import native
+    case = _mixed_case(8, Z=64, seed=18)
+    for threads, words in ((48, 1), (2048, 1), (96, 2)):  # not a multiple of 32 * words, or above 1024
+        with pytest.raises(native.LdpcError) as ei:
+            _run(case, 5, words=words, threads=threads)
+        assert ei.value.code == native.LDPC_EINVAL and "threads" in str(ei.value)
+
+
+@pytest.mark.parametrize("words", [1, 2, 4])
+@pytest.mark.parametrize("stall", [0, 5])
+def test_interactive_launch_every_group_width(words, stall):
+    """All rounds in one launch (ldpc_reconcile_interactive) at every group
+    width: frames failing a round restart in their lane with more bits
+    revealed; against the oracle's protocol frame by frame."""
+    import math
+    from oracle import protocol as oproto
+    from paper_1903_10107_gb300.decoder import QCCode
+    case = _mixed_case(47, seed=51, f_target=1.1, scale=1 / 0.29)
+    base, Z, n, m, q = case["base"], case["Z"], case["n"], case["m"], case["q"]
+    R, df, T = 4, 0.2, 40
+    p0, s0 = case["npn"].astype(np.int64), case["ns"].astype(np.int64)
+    rev = np.zeros((len(q), R + 1), np.int64)
+    for r in range(R):
+        for f in range(len(q)):
+            key_now = n - p0[f] - s0[f] - max(int(rev[f, r]) - int(p0[f]), 0)
+            rev[f, r + 1] = rev[f, r] + oproto.reveal_step(df, int(key_now), float(q[f]))
+    code = QCCode(base, Z)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    bits, iters, ok, rounds = code.reconcile_interactive(
+        c(case["yb"]), device_mags(q, case["scale"]), c(inputs.pack_bits(case["syn_u"])), T, c(case["rank"]),
+        c(case["ns"]), c(case["npn"]), c(case["xa"]), c(rev.astype(np.int32)), stall_window=stall, words=words)
+    torch.cuda.synchronize()
+    ref = oproto.interactive(base, Z, inputs.tiebreak_permutation(n, 51), inputs.unpack_bits(case["xa"], n),
+                             inputs.unpack_bits(case["yb"], n), q, 1.1, df, R, T, case["scale"], stall_window=stall)
+    assert np.array_equal(inputs.unpack_bits(bits.cpu().numpy(), n), ref["bits"])
+    assert np.array_equal(ok.cpu().numpy(), ref["ok"]) and np.array_equal(rounds.cpu().numpy(), ref["rounds"])
+    assert np.array_equal(iters.cpu().numpy(), ref["iters"])
+    assert len(set(ref["rounds"].tolist())) >= 3  # frames finished in several different rounds
+    assert np.array_equal(rev[np.arange(len(q)), ref["rounds"]], ref["revealed"])

@@ -32,7 +32,7 @@ def test_mixed_rate_batch_graph_matches_oracle():
     p, s = rec.plan(q, 1.5)
     c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     syn = rec.code.syndrome(c(xa))
-    mrb = MixedRateBatch(rec, 50).bind(c(yb), syn, c(q), c(p), c(s), c(xa))
+    mrb = MixedRateBatch(rec, 50).bind(c(yb), syn, c(rec.magnitudes(q)), c(p), c(s), c(xa))
     assert mrb.graph is not None
     for t in mrb.out:
         t.zero_()
@@ -46,36 +46,36 @@ def test_mixed_rate_batch_graph_matches_oracle():
     assert np.array_equal(inputs.unpack_bits(bits, n), ob)
 
 
-def test_interactive_protocol_matches_oracle_per_round_state():
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("stall", [0, 6])
+def test_interactive_protocol_matches_the_oracle_protocol(stall, fused):
+    """Every round's launch over the frames still failing, the reveals between
+    rounds and the final efficiency, against the oracle's protocol run on the
+    same frames: bits, summed iterations, flags, rounds, revealed bits, key
+    bits and f, frame by frame."""
+    from oracle import protocol as oproto
     from paper_1903_10107_gb300.pipeline import InteractiveProtocol, Reconciler
     B = 48
     base, Z, n, m, q, xa, yb, tb = _code_and_frames(B, seed=9)
     rec = Reconciler(base, Z, tb, llr_scale=SCALE)
     c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     syn = rec.code.syndrome(c(xa))
-    proto = InteractiveProtocol(rec, 40, f_start=1.1, df=0.15, max_rounds=5)
-    res = proto.run(c(yb), syn, q, c(xa))
+    proto = InteractiveProtocol(rec, 40, f_start=1.1, df=0.15, max_rounds=5, stall_window=stall, fused=fused)
+    res = proto.run(c(yb), syn, q, c(xa), timing=True)
     assert res["rounds"].max() >= 1 and res["revealed"].max() > 0
-    # every frame's final result equals the oracle decode at its final reveal state
-    rank = orate.position_rank(base, Z, tb)
+    assert res["launches"] == (1 if fused else res["rounds"].max() + 1) and res["kernel_s"] > 0
     xa_u = inputs.unpack_bits(xa, n)
-    syn_u = orc.syndrome(base, Z, xa_u)
-    st = []
-    for f in range(B):
-        p0, s0 = orate.rate_plan(n, m, float(q[f]), 1.1)
-        r = int(res["revealed"][f])
-        st.append(orate.position_states(rank, max(p0 - r, 0), s0 + r))
-        # efficiency bookkeeping against the closed form: leak / (key * h(q))
-        rp = min(r, p0)
-        key = n - p0 - s0 - (r - rp)
-        f_ref = (m - p0 + rp) / (key * orate.binary_entropy(float(q[f])))
-        assert abs(res["f"][f] - f_ref) < 1e-9 and res["key_bits"][f] == key
-    llr = orc.llr_frames(inputs.unpack_bits(yb, n), q, np.stack(st), xa_u, scale=SCALE)
-    ob, oi, oo, _ = orc.decode(base, Z, llr, syn_u, 40)
-    assert np.array_equal(res["ok"], oo)
-    assert np.array_equal(inputs.unpack_bits(res["bits"], n), ob)
-    # frames that needed more rounds ended at a higher efficiency
-    assert (res["f"][res["rounds"] > 0] > 1.1).all()
+    ref = oproto.interactive(base, Z, tb, xa_u, inputs.unpack_bits(yb, n), q, 1.1, 0.15, 5, 40, SCALE,
+                             stall_window=stall)
+    assert np.array_equal(inputs.unpack_bits(res["bits"], n), ref["bits"])
+    for k in ("ok", "iters", "rounds", "revealed", "key_bits"):
+        assert np.array_equal(np.asarray(res[k]), np.asarray(ref[k])), k
+    np.testing.assert_allclose(res["f"], ref["f"], rtol=1e-12)
+    # the host-buffer entry gives the same results and counts its copies
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hres, h2d, d2h = proto.run_host(pin(yb), syn.cpu().pin_memory(), q, pin(xa))
+    assert np.array_equal(hres["bits"], res["bits"]) and np.array_equal(hres["iters"], res["iters"])
+    assert h2d >= yb.nbytes + syn.numel() + xa.nbytes and d2h >= res["bits"].nbytes + 5 * B
 
 
 def test_host_buffer_path_matches_oracle_and_counts_bytes():
@@ -91,7 +91,7 @@ def test_host_buffer_path_matches_oracle_and_counts_bytes():
     (bits, iters, ok), h2d, d2h = rec.reconcile_host(pin(yb), syn.pin_memory(), pin(q), 50, pin(p), pin(s),
                                                      pin(xa), persistent=True)
     torch.cuda.synchronize()
-    assert h2d == yb.nbytes + syn.numel() + q.nbytes + p.nbytes + s.nbytes + xa.nbytes + 4 * B
+    assert h2d == yb.nbytes + syn.numel() + B + p.nbytes + s.nbytes + xa.nbytes + 4 * B  # one magnitude byte per frame
     assert d2h == bits.numel() + 4 * B + B
     rank = orate.position_rank(base, Z, tb)
     st = np.stack([orate.position_states(rank, int(p[f]), int(s[f])) for f in range(B)])

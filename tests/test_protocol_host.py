@@ -25,8 +25,8 @@ class FakeCode:
         self.succeed_at = np.asarray(succeed_at)
         self.calls = []
 
-    def reconcile_persistent(self, bob, qber, syn, max_iter, rank=None, n_short=None, n_punct=None, known=None,
-                             frame_list=None, llr_scale=None, words=0, ctas_per_sm=0, out=None):
+    def reconcile_persistent(self, bob, llr_mag, syn, max_iter, rank=None, n_short=None, n_punct=None, known=None,
+                             frame_list=None, stall_window=0, words=0, ctas_per_sm=0, threads=0, out=None):
         rnd = len(self.calls)
         frames = frame_list.numpy().copy()
         self.calls.append(dict(frames=frames, n_punct=n_punct.numpy().copy(), n_short=n_short.numpy().copy()))
@@ -42,9 +42,10 @@ def test_rounds_reveals_and_efficiency():
     q = np.array([0.01, 0.02, 0.03, 0.05, 0.07, 0.08])
     succeed_at = np.array([0, 1, 3, 2, 9, 5])  # frame 4 never succeeds within the rounds
     code = FakeCode(n, m, succeed_at)
-    rec = types.SimpleNamespace(code=code, rank=torch.zeros(n, dtype=torch.int32), llr_scale=3.0)
+    rec = types.SimpleNamespace(code=code, rank=torch.zeros(n, dtype=torch.int32), llr_scale=3.0,
+                                magnitudes=lambda qq: np.zeros(len(qq), np.int8))
     df, max_rounds, f0 = 0.1, 6, 1.1
-    proto = InteractiveProtocol(rec, max_iter=50, f_start=f0, df=df, max_rounds=max_rounds)
+    proto = InteractiveProtocol(rec, max_iter=50, f_start=f0, df=df, max_rounds=max_rounds, fused=False)
     B = q.size
     res = proto.run(torch.zeros((B, code.nbytes), dtype=torch.uint8), torch.zeros((B, m // 8), dtype=torch.uint8),
                     q, torch.zeros((B, code.nbytes), dtype=torch.uint8))
@@ -84,3 +85,50 @@ def test_rounds_reveals_and_efficiency():
     assert np.all(res["f"][punct_only] >= (f_start + df * last - 1e-9)[punct_only])
     grow = f_start * (1.0 / (1.0 - df * rate.h2(q))) ** last
     assert np.all(res["f"][~punct_only] >= grow[~punct_only] - 1e-9)
+
+
+class FakeFusedCode(FakeCode):
+    """The one-launch form: records the reveal table and reports, per frame,
+    success in round succeed_at[f] (if within the rounds), iterations summed
+    as 10 + r per round r decoded."""
+
+    def reconcile_interactive(self, bob, llr_mag, syn, max_iter, rank, n_short, n_punct, known, reveal,
+                              frame_list=None, stall_window=0, words=0, ctas_per_sm=0, threads=0, out=None):
+        R = reveal.shape[1] - 1
+        self.calls.append(dict(frames=frame_list.numpy().copy(), n_short=n_short.numpy().copy(),
+                               n_punct=n_punct.numpy().copy(), reveal=reveal.numpy().copy()))
+        B = n_short.shape[0]
+        last = np.minimum(self.succeed_at, R)
+        ok = torch.from_numpy((self.succeed_at <= R).astype(np.uint8))
+        iters = torch.from_numpy(np.array([sum(10 + r for r in range(int(k) + 1)) for k in last], dtype=np.int32))
+        bits = torch.zeros((B, self.nbytes), dtype=torch.uint8)
+        return bits, iters, ok, torch.from_numpy(last.astype(np.int32))
+
+
+def test_fused_rounds_take_the_same_reveals_as_separate_rounds():
+    """One launch for all rounds: the reveal table handed to it holds exactly
+    the reveals the round-by-round protocol applies, and the results (rounds,
+    revealed bits, key bits, efficiency, summed iterations) are the same."""
+    n, m = 4096, 1024
+    q = np.array([0.01, 0.02, 0.03, 0.05, 0.07, 0.08])
+    succeed_at = np.array([0, 1, 3, 2, 9, 5])
+    kw = dict(max_iter=50, f_start=1.1, df=0.1, max_rounds=6)
+    mk = lambda code: types.SimpleNamespace(code=code, rank=torch.zeros(n, dtype=torch.int32), llr_scale=3.0,
+                                            magnitudes=lambda qq: np.zeros(len(qq), np.int8))
+    B = q.size
+    args = (torch.zeros((B, n // 8), dtype=torch.uint8), torch.zeros((B, m // 8), dtype=torch.uint8), q,
+            torch.zeros((B, n // 8), dtype=torch.uint8))
+    sep = InteractiveProtocol(mk(FakeCode(n, m, succeed_at)), fused=False, **kw).run(*args)
+    fused_code = FakeFusedCode(n, m, succeed_at)
+    fus = InteractiveProtocol(mk(fused_code), **kw).run(*args)
+    (call,) = fused_code.calls  # a single launch
+    p0, s0 = rate.plan(n, m, q, 1.1)
+    assert np.array_equal(call["n_punct"], p0) and np.array_equal(call["n_short"], s0)
+    assert np.array_equal(call["frames"], hardest_first(p0, s0, q))
+    rev = call["reveal"]
+    assert rev.shape == (B, 7) and (rev[:, 0] == 0).all() and (np.diff(rev, axis=1) > 0).all()
+    for k in ("rounds", "revealed", "key_bits", "iters", "ok"):
+        assert np.array_equal(np.asarray(sep[k]), np.asarray(fus[k])), k
+    np.testing.assert_allclose(sep["f"], fus["f"], rtol=1e-12)
+    # every frame's revealed count is the table's entry at its last round
+    assert np.array_equal(fus["revealed"], rev[np.arange(B), fus["rounds"]])

@@ -4,8 +4,9 @@ process whose GPU memory belongs to another allocator's pool, a loop that
 cannot afford an allocation's synchronisation).
 
 It is called through the C ABI and must return exactly what
-ldpc_decode_batch returns, on two calls in a row (the second call finds the
-first call's leftovers in the shared fixed scratch).  Collected last on
+ldpc_decode_batch returns, and what the CPU oracle computes, on two calls in
+a row (the second call finds the first call's leftovers in the shared fixed
+scratch).  Collected last on
 purpose: a failure here leaves every other test already run."""
 import numpy as np
 import pytest
@@ -21,9 +22,9 @@ def _inputs(base, Z, B, q, seed):
     n = base.shape[1] * Z
     xa = inputs.alice_keys(B, n, seed)
     yb = xa ^ inputs.bsc_noise(B, n, q, seed)
-    syn = inputs.pack_bits(orc.syndrome(base, Z, inputs.unpack_bits(xa, n)))
+    syn_u = orc.syndrome(base, Z, inputs.unpack_bits(xa, n))
     llr = orc.llr_frames(inputs.unpack_bits(yb, n), q)
-    return torch.from_numpy(llr).cuda(), torch.from_numpy(syn).cuda()
+    return torch.from_numpy(llr).cuda(), torch.from_numpy(inputs.pack_bits(syn_u)).cuda(), llr, syn_u
 
 
 def _outputs(code, B):
@@ -41,7 +42,7 @@ def test_noalloc_decode_matches_decode_batch_on_two_calls():
     st = torch.cuda.current_stream().cuda_stream
     # two different batches (sizes, noise) back to back through the fixed scratch
     for B, q, seed in ((150, 0.03, 11), (61, 0.02, 12)):
-        llr, syn = _inputs(base, w.Z, B, q, seed)
+        llr, syn, llr_np, syn_u = _inputs(base, w.Z, B, q, seed)
         ref = [t.cpu().numpy() for t in code.decode(llr, syn, w.max_iter)]
         out = _outputs(code, B)
         native.ldpc_decode_batch_noalloc(code.handle, llr.data_ptr(), syn.data_ptr(), B, w.max_iter,
@@ -50,6 +51,10 @@ def test_noalloc_decode_matches_decode_batch_on_two_calls():
         got = [t.cpu().numpy() for t in out]
         for a, b in zip(ref, got):
             assert np.array_equal(a, b)  # integer results: bit-exact is the tolerance
+        # and directly against the CPU oracle, so the check stands on its own
+        ob, oi, oo, _ = orc.decode(base, w.Z, llr_np, syn_u, w.max_iter)
+        assert np.array_equal(inputs.unpack_bits(got[0], code.n), ob)
+        assert np.array_equal(got[1], oi) and np.array_equal(got[2], oo)
         assert 0 < got[2].sum() < B  # both decoded and failing frames were exercised
 
 
