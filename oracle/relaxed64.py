@@ -20,7 +20,20 @@ listed in section 2):
 There is no saturation, so Algorithm 2's guard does not apply and the
 variable-node update is the plain Eq. 9.  The loss is the mean binary cross
 entropy of the final soft values against Alice's bits (soft value E > 0
-means bit 0).  A degree-1 row sends the constant EMPTY (the empty box-plus).
+means bit 0).
+
+A degree-1 row's check node has no other edge: its box-plus is over the
+empty set, +infinity, and the integer decoder sends MSG_max (its largest
+magnitude, 127 LSB).  +infinity cannot be carried in floating point through
+the next E - L of the same edge (it would give infinity - infinity), so the
+relaxation sends the finite stand-in EMPTY (a reading).  EMPTY = 50 nats
+exceeds the integer decoder's MSG_max in nats at every LLR step used here
+(127 * 0.29 = 36.8 at the table's own step, 127 / 8 = 15.9 at 8 LSB per
+nat), and well before that nothing else the decoder computes depends on it:
+box-plus against such a magnitude returns the other operand up to a term of
+order exp(-(EMPTY - other)/kappa).  ``decode``, ``loss`` and
+``loss_and_grad`` take it as a parameter so that tests can check that
+independence.
 
 ``decode`` is numpy; ``loss_and_grad`` builds the same computation from
 torch fp64 CPU operations so that autograd supplies a reference gradient.
@@ -81,7 +94,7 @@ def _exclusive_boxplus(a, bp, xp):
     return xp.stack(outs, axis=1)
 
 
-def decode(base, Z, llr, syn, iters, alpha=None, gamma=None, stop=False, kappa=1.0):
+def decode(base, Z, llr, syn, iters, alpha=None, gamma=None, stop=False, kappa=1.0, empty=EMPTY):
     """Relaxed layered decoding.  llr: float [B][n] (positive = bit 0),
     syn: 0/1 [B][m].  alpha, gamma: [iters][classes] or None (1, 0).
     Returns the final soft values E [B][n] (and, with stop=True, the
@@ -106,7 +119,7 @@ def decode(base, Z, llr, syn, iters, alpha=None, gamma=None, stop=False, kappa=1
             al = 1.0 if alpha is None else alpha[t, cls[i]]
             ga = 0.0 if gamma is None else gamma[t, cls[i]]
             if d == 1:
-                mag = np.full_like(mag, EMPTY)
+                mag = np.full_like(mag, empty)
             mag = al * np.maximum(mag - ga, 0.0)
             Ln = S * s * mag
             E[:, J] = v + Ln
@@ -123,7 +136,7 @@ def decode(base, Z, llr, syn, iters, alpha=None, gamma=None, stop=False, kappa=1
     return (E, done) if stop else E
 
 
-def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma, kappa=1.0):
+def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma, kappa=1.0, empty=EMPTY):
     """Mean BCE of the final E against Alice's bits, and its gradient with
     respect to alpha and gamma, by torch fp64 autograd on the CPU."""
     import torch
@@ -152,7 +165,7 @@ def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma, kappa=1.0):
             s = torch.where(v < 0, -1.0, 1.0).to(torch.float64)
             S = ssign[:, i * Z:(i + 1) * Z][:, None, :] * torch.prod(s, dim=1, keepdim=True)
             if d == 1:
-                mag = torch.full_like(v, EMPTY)
+                mag = torch.full_like(v, empty)
             else:
                 mag = _exclusive_boxplus(v.abs(), bp, torch)
             mag = al[t, cls[i]] * torch.relu(mag - ga[t, cls[i]])
@@ -165,3 +178,11 @@ def loss_and_grad(base, Z, llr, syn, xa, alpha, gamma, kappa=1.0):
     loss = torch.nn.functional.softplus(-sgn * E).mean()
     loss.backward()
     return float(loss.detach()), al.grad.numpy().copy(), ga.grad.numpy().copy(), E.detach().numpy()
+
+
+def loss(base, Z, llr, syn, xa, iters, alpha, gamma, kappa=1.0, empty=EMPTY):
+    """The same mean cross entropy from ``decode`` (numpy fp64), for finite
+    differences."""
+    E = decode(base, Z, llr, syn, iters, alpha, gamma, kappa=kappa, empty=empty)
+    x = -(1.0 - 2.0 * np.asarray(xa, dtype=np.float64)) * E
+    return float(np.mean(np.maximum(x, 0.0) + np.log1p(np.exp(-np.abs(x)))))

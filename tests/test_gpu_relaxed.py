@@ -1,6 +1,16 @@
 """The FP32 relaxed decoder and its hand-written adjoint against the FP64
-reference: forward within 1e-4 relative, gradient within 1e-3 relative, and
-the adjoint against finite differences of the GPU loss."""
+reference: forward soft values within 1e-4 relative, the loss within 1e-4,
+and every gradient component within 1e-3 relative,
+
+    |g - g64| <= 1e-3 * max(|g64|, FLOOR * max|g64|),   FLOOR = 0.01,
+
+i.e. components below 1 % of the largest are held to 1e-5 of the largest
+(an FP32 sum of many terms of both signs cannot give a tiny component to a
+relative 1e-3; measured at the training shape, 20 iterations on the n = 4096
+code: 6e-4 with this floor, 1.8e-3 on a component 1100 times below the
+largest without it).  The adjoint is also checked against central finite
+differences of the FP64 loss per parameter and against finite differences
+of the GPU loss along a direction."""
 import numpy as np
 import pytest
 
@@ -9,6 +19,16 @@ from paper_1903_10107_gb300 import inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+
+FLOOR = 0.01
+
+
+def _assert_grad_close(got, ref, tol=1e-3):
+    got, ref = np.ravel(got), np.ravel(ref)
+    scale = np.maximum(np.abs(ref), FLOOR * np.abs(ref).max())
+    err = np.abs(got - ref) / scale
+    assert err.max() <= tol, (err.max(), int(err.argmax()), got[err.argmax()], ref[err.argmax()])
 
 
 def _case(Mb=4, Nb=12, Z=16, B=6, seed=0, mu=2.0, sigma=1.5):
@@ -61,9 +81,7 @@ def test_gradient_matches_fp64_reference(kappa):
     loss, E, g_al, g_ga, _, _ = _gpu(base, Z, llr, syn, xa, al, ga, kappa, T)
     l64, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=kappa)
     assert abs(loss - l64) <= 1e-4 * abs(l64)
-    ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
-    got = np.concatenate([g_al.ravel(), g_ga.ravel()])
-    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
+    _assert_grad_close(np.concatenate([g_al.ravel(), g_ga.ravel()]), np.concatenate([r_al.ravel(), r_ga.ravel()]))
 
 
 def test_gradient_matches_finite_differences_of_gpu_loss():
@@ -135,9 +153,7 @@ def test_forward_and_gradient_on_special_shapes(case):
     assert rel.max() <= 1e-4, rel.max()
     l64, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=kappa)
     assert abs(loss - l64) <= 1e-4 * abs(l64)
-    ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
-    got = np.concatenate([g_al.ravel(), g_ga.ravel()])
-    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
+    _assert_grad_close(np.concatenate([g_al.ravel(), g_ga.ravel()]), np.concatenate([r_al.ravel(), r_ga.ravel()]))
 
 
 @pytest.mark.parametrize("Nb", [18, 24, 32])
@@ -162,9 +178,7 @@ def test_every_unroll_width_against_fp64(Nb):
     assert rel.max() <= 1e-4, rel.max()
     l64, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=0.431)
     assert abs(loss - l64) <= 1e-4 * abs(l64)
-    ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
-    got = np.concatenate([g_al.ravel(), g_ga.ravel()])
-    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
+    _assert_grad_close(np.concatenate([g_al.ravel(), g_ga.ravel()]), np.concatenate([r_al.ravel(), r_ga.ravel()]))
 
 
 def test_larger_code_two_frames_per_cta():
@@ -182,6 +196,61 @@ def test_larger_code_two_frames_per_cta():
     assert rel.max() <= 1e-4, rel.max()
     l64, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=0.431)
     assert abs(loss - l64) <= 1e-4 * abs(l64)
-    ref = np.concatenate([r_al.ravel(), r_ga.ravel()])
-    got = np.concatenate([g_al.ravel(), g_ga.ravel()])
-    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref), (np.linalg.norm(got - ref), np.linalg.norm(ref))
+    _assert_grad_close(np.concatenate([g_al.ravel(), g_ga.ravel()]), np.concatenate([r_al.ravel(), r_ga.ravel()]))
+
+
+def _training_shape_case(B=4, sigma=0.5, T=20, seed=7):
+    """The training workload's shape: the n = 4096 code, QBER U(2 %, 4 %),
+    20 iterations, the temperature of 8 LSB per nat.  Channel LLRs are the
+    BSC's plus N(0, sigma^2) noise (Gaussian relaxation): continuous inputs,
+    so that no soft value sits exactly on a sign or relu kink."""
+    from oracle import core as orc
+    from paper_1903_10107_gb300.relaxed import bsc_llr_nats, kappa_for_scale
+    w = inputs.WORKLOADS["n4096_relaxed_q02_04"]
+    base = w.base()
+    xa, yb, q = w.frames(B, 0)
+    xa_u, yb_u = inputs.unpack_bits(xa, w.n), inputs.unpack_bits(yb, w.n)
+    g = np.random.default_rng(seed)
+    llr = (bsc_llr_nats(yb_u, q) + g.normal(0, sigma, size=(B, w.n))).astype(np.float32)
+    syn = orc.syndrome(base, w.Z, xa_u)
+    C = len(rx.degree_classes(base)[1])
+    al = g.uniform(0.7, 1.1, (T, C)).astype(np.float32).astype(np.float64)
+    ga = g.uniform(0.05, 0.3, (T, C)).astype(np.float32).astype(np.float64)
+    assert T == w.max_iter
+    return base, w.Z, llr, syn, xa_u, al, ga, kappa_for_scale(8.0)
+
+
+def test_training_shape_forward_and_every_gradient_component():
+    base, Z, llr, syn, xa, al, ga, kappa = _training_shape_case()
+    loss, E, g_al, g_ga, _, _ = _gpu(base, Z, llr, syn, xa, al, ga, kappa, al.shape[0])
+    l64, r_al, r_ga, E64 = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=kappa)
+    assert abs(loss - l64) <= 1e-4 * abs(l64)
+    rel = np.abs(E - E64) / np.maximum(np.abs(E64), 1.0)
+    assert rel.max() <= 1e-4, rel.max()
+    _assert_grad_close(g_al, r_al)
+    _assert_grad_close(g_ga, r_ga)
+    _assert_grad_close(np.concatenate([g_al.ravel(), g_ga.ravel()]), np.concatenate([r_al.ravel(), r_ga.ravel()]))
+
+
+def test_training_shape_gradient_against_central_differences_per_parameter():
+    """Central differences of the FP64 loss, one parameter at a time, at
+    first, middle and last iterations and at the smallest, a middle and the
+    largest degree class.  The step is 1e-7: the loss is only piecewise
+    smooth (soft values change sign, relu edges move), and wider steps cross
+    kinks (1e-4 was off by up to 15 % for first-iteration parameters; 1e-7
+    agrees with autograd to a few 1e-6)."""
+    base, Z, llr, syn, xa, al, ga, kappa = _training_shape_case()
+    T, C = al.shape
+    _, _, g_al, g_ga, _, _ = _gpu(base, Z, llr, syn, xa, al, ga, kappa, T)
+    _, r_al, r_ga, _ = rx.loss_and_grad(base, Z, llr.astype(np.float64), syn, xa, al, ga, kappa=kappa)
+    scale = FLOOR * max(np.abs(r_al).max(), np.abs(r_ga).max())
+    eps = 1e-7
+    for t, c in ((0, 0), (0, C - 1), (T // 2, C // 2), (T - 1, 0), (T - 1, C - 1), (5, min(1, C - 1))):
+        for which, gpu, ref in (("alpha", g_al, r_al), ("gamma", g_ga, r_ga)):
+            def L(sign):
+                a2, g2 = al.copy(), ga.copy()
+                (a2 if which == "alpha" else g2)[t, c] += sign * eps
+                return rx.loss(base, Z, llr.astype(np.float64), syn, xa, T, a2, g2, kappa=kappa)
+            fd = (L(1) - L(-1)) / (2 * eps)
+            assert abs(fd - ref[t, c]) <= 1e-4 * max(abs(ref[t, c]), scale), (which, t, c, fd, ref[t, c])
+            assert abs(gpu[t, c] - fd) <= 1e-3 * max(abs(fd), scale), (which, t, c, gpu[t, c], fd)

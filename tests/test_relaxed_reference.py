@@ -116,3 +116,64 @@ def test_tree_code_converges_to_brute_force_posterior():
             l0 = np.logaddexp.reduce(logw[coset[:, j] == 0])
             l1 = np.logaddexp.reduce(logw[coset[:, j] == 1])
             assert abs(E[f, j] - (l0 - l1)) < 1e-9, (f, j, E[f, j], l0 - l1)
+
+
+def _degree_one_case(Z=8, B=4, seed=21):
+    """Rows of degree 1 (two of them), 2, 5 and 9 on 12 block columns."""
+    g = np.random.default_rng(seed)
+    Nb = 12
+    base = np.full((5, Nb), -1, dtype=np.int32)
+    for row, cols in ((0, [3]), (1, [7]), (2, [0, 5]), (3, [1, 2, 4, 8, 11]), (4, [0, 3, 5, 6, 7, 8, 9, 10, 11])):
+        base[row, cols] = g.integers(0, Z, size=len(cols))
+    from oracle import core as orc
+    n = Nb * Z
+    xa = g.integers(0, 2, size=(B, n)).astype(np.uint8)
+    syn = orc.syndrome(base, Z, xa)
+    llr = (1 - 2.0 * xa) * 1.5 + g.normal(0, 1.5, size=(B, n))
+    return base, Z, llr, syn, xa
+
+
+def test_empty_boxplus_stand_in_acts_as_infinity():
+    """A degree-1 row sends EMPTY in place of the empty box-plus (+infinity).
+    Beyond about 30 nats nothing else the decoder computes depends on the
+    value: every soft value of a variable outside the degree-1 rows, the
+    hard decisions and the loss agree to 1e-9 between EMPTY = 40, 50 and
+    1000.  The degree-1 rows' own variables get soft values of magnitude
+    about EMPTY whose sign does not depend on it (their check pins them).
+    Far below the other magnitudes (EMPTY = 5) the stand-in is no longer
+    neutral."""
+    base, Z, llr, syn, xa = _degree_one_case()
+    T, kappa = 6, 0.431
+    C = len(rx.degree_classes(base)[1])
+    al, ga = np.full((T, C), 0.9), np.full((T, C), 0.1)
+    deg1 = np.zeros(base.shape[1] * Z, bool)
+    for i in np.flatnonzero((base >= 0).sum(axis=1) == 1):
+        k = int(np.flatnonzero(base[i] >= 0)[0])
+        deg1[k * Z:(k + 1) * Z] = True
+    E = {e: rx.decode(base, Z, llr, syn, T, al, ga, kappa=kappa, empty=e) for e in (5.0, 40.0, 50.0, 1000.0)}
+    Ls = {e: rx.loss(base, Z, llr, syn, xa, T, al, ga, kappa=kappa, empty=e) for e in (40.0, 50.0, 1000.0)}
+    for e in (40.0, 1000.0):
+        assert np.allclose(E[e][:, ~deg1], E[50.0][:, ~deg1], rtol=1e-9, atol=1e-9)
+        assert np.array_equal(E[e] < 0, E[50.0] < 0)
+        assert abs(Ls[e] - Ls[50.0]) <= 1e-9 * Ls[50.0]
+    # the degree-1 variables: |E| grows with the stand-in (their row pins them) and keeps its sign
+    assert np.all(np.abs(E[1000.0][:, deg1]) > 500) and np.array_equal(E[1000.0][:, deg1] < 0, E[50.0][:, deg1] < 0)
+    # far below the decoder's other magnitudes the stand-in is not neutral any more
+    assert not np.allclose(E[5.0][:, ~deg1], E[50.0][:, ~deg1], rtol=1e-6, atol=1e-6)
+
+
+def test_empty_stand_in_exceeds_the_integer_decoders_largest_message():
+    """EMPTY is at least the integer decoder's MSG_max (127 LSB) in nats at
+    the LLR steps the workloads use: the table's own 0.29 nat and 1/8 nat."""
+    assert rx.EMPTY >= 127 * 0.29 and rx.EMPTY >= 127 / 8.0
+
+
+def test_numpy_loss_equals_autograd_loss():
+    base, Z, llr, syn, xa = _degree_one_case(seed=22)
+    T = 4
+    C = len(rx.degree_classes(base)[1])
+    g = np.random.default_rng(5)
+    al, ga = g.uniform(0.7, 1.1, (T, C)), g.uniform(0.0, 0.3, (T, C))
+    l_np = rx.loss(base, Z, llr, syn, xa, T, al, ga, kappa=0.6)
+    l_t, _, _, _ = rx.loss_and_grad(base, Z, llr, syn, xa, al, ga, kappa=0.6)
+    assert abs(l_np - l_t) <= 1e-12 * abs(l_t)
