@@ -222,6 +222,53 @@ int ldpc_reconcile_interactive(const ldpc_code* code, const uint8_t* bob_bits, c
                                uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, int32_t* out_rounds,
                                void* stream);
 
+/* Bytes of the lane-state buffer that ldpc_reconcile_epoch needs for a launch
+ * shape (words 1, 2 or 4 explicitly; ctas_per_sm and threads as in
+ * ldpc_reconcile_persistent), and the grid that shape runs (`grid` may be
+ * NULL).  Host only. */
+int ldpc_epoch_state_bytes(const ldpc_code* code, int words, int ctas_per_sm, int threads, size_t* bytes,
+                           int* grid);
+
+/* One epoch of a continuously batched persistent decode, for serving: the
+ * persistent decoder of ldpc_reconcile_persistent where every CTA runs at
+ * most `epoch_iters` decoder iterations and then saves its lanes -- each
+ * frame's iteration count and stall-rule state, its soft values and
+ * syndrome bits -- into `lane_state` and returns.  Its messages stay in the
+ * code handle's arena, in the region of the same CTA.  The next call with
+ * `resume` = 1 restores the lanes and continues their frames where they
+ * stopped; lanes that are free (their frame finished) take frames from this
+ * call's frame_list.  Frames thus join and leave between epochs while the
+ * others' decoding state stays on the device; nothing on the device waits
+ * for the host.  A frame's results equal those of one
+ * ldpc_reconcile_persistent call, however its decode is split.
+ *   Per-frame arrays (bob_bits ... target_syndrome, outputs) are indexed by
+ *       frame id in [0, batch) as in ldpc_reconcile_persistent.  A frame's
+ *       inputs are read once, when a lane takes it; its outputs are written
+ *       when it finishes (out_iters >= 1 then, so a caller that zeroes
+ *       out_iters at admission can see which frames are done).
+ *   frame_list, list_len : the frames this epoch may start (list_len >= 0);
+ *       frames a lane took are counted in *out_claimed.
+ *   epoch_iters >= 1 : iterations per CTA in this call.
+ *   resume : 0 for the first epoch of a lane-state buffer (every lane
+ *       free), 1 afterwards.  Every epoch of one buffer must use the same
+ *       code handle, words, ctas_per_sm and threads, and no other decode may
+ *       use that handle in between (it owns the messages).
+ *   lane_state : device, 256-byte aligned, lane_state_bytes >=
+ *       ldpc_epoch_state_bytes(code, words, ctas_per_sm, threads).
+ *   words : 1, 2 or 4 (no automatic choice: it fixes the lane layout).
+ *   out_claimed : device, int32[1]: how many entries of frame_list were
+ *       handed to a lane (claims past the list's end are counted too, so
+ *       the frames taken are the first min(*out_claimed, list_len)); the
+ *       rest are for a later epoch.
+ * The stall window applies as in ldpc_reconcile_persistent; the claim-hold
+ * rule does not (each epoch's list is short). */
+int ldpc_reconcile_epoch(const ldpc_code* code, const uint8_t* bob_bits, const int8_t* llr_mag, const int32_t* rank,
+                         const int32_t* n_short, const int32_t* n_punct, const uint8_t* known,
+                         const uint8_t* target_syndrome, int batch, const int32_t* frame_list, int list_len,
+                         int max_iter, int stall_window, int epoch_iters, int resume, void* lane_state,
+                         size_t lane_state_bytes, int words, int ctas_per_sm, int threads, uint8_t* out_bits,
+                         int32_t* out_iters, uint8_t* out_ok, int32_t* out_claimed, void* stream);
+
 /* Grow the scratch arena now for a persistent decode of `list_len` frames
  * with the given `words`, `ctas_per_sm` and `threads` (0 = automatic, as in
  * ldpc_reconcile_persistent), so that the decode itself allocates nothing

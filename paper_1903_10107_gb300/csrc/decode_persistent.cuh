@@ -50,6 +50,15 @@ struct PersistArgs {
     const int32_t* reveal;
     int max_rounds;
     int32_t* out_rounds;
+    // Epoch mode (serving; epoch_iters > 0): every CTA runs at most epoch_iters iterations, then saves its
+    // lanes -- lane records, soft-value image, syndrome nibbles, lane masks -- and returns; its messages
+    // stay in its own arena region.  With resume set a CTA first restores what it saved, then fills its
+    // free lanes from this launch's frame list.  The grid is the same in every epoch.
+    int epoch_iters, resume;
+    int32_t* lane_save;   // [grid][4W][kLaneRec]
+    uint32_t* word_save;  // [grid][2W]: active and fresh masks
+    uint32_t* e_save;     // [grid][n W]
+    uint8_t* syn_save;    // [grid][m W]
     uint32_t* msg;
     int* queue;  // [0] frames claimed, [1] frames finished, [2..3] their iterations (64 bit); zeroed per launch
 };
@@ -67,6 +76,25 @@ __device__ __forceinline__ int frame_of(const PersistArgs& A, int slot) {
 // mean iteration count).
 constexpr int kHoldAfter = 16;
 constexpr int kHoldMinDone = 64;
+
+// Integers per saved lane: frame, iterations, round, earlier rounds' iterations, fewest unsatisfied checks
+// and its iteration, LLR magnitude, shortened and punctured counts.
+constexpr int kLaneRec = 9;
+
+// Bytes of the epoch-mode save area of `grid` CTAs, and the offsets of its parts.
+struct EpochLayout {
+    size_t lanes, words, soft, syn, total;
+};
+__host__ __device__ inline EpochLayout epoch_layout(int n, int m, int W, int grid) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    EpochLayout L;
+    L.lanes = 0;
+    L.words = up(L.lanes + (size_t)grid * 4 * W * kLaneRec * sizeof(int32_t));
+    L.soft = up(L.words + (size_t)grid * 2 * W * sizeof(uint32_t));
+    L.syn = up(L.soft + (size_t)grid * n * W * sizeof(uint32_t));
+    L.total = up(L.syn + (size_t)grid * m * W);
+    return L;
+}
 
 template <int MAXH, int P, int W, int MAXT>
 __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
@@ -91,31 +119,89 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
     const int rt = q / P, RT = T / (W * P), QT = T / W;
 
     const ldpc_dev::Tables TB = ldpc_dev::load_tables(s_tab, A.tab, Mb, nblk, Z, W, tid, T);
-    if (tid == 0) s_base = atomicAdd(A.queue, NL);
+    const bool epoch = A.epoch_iters > 0;
+    const int b = blockIdx.x;
     if (tid < W) {
-        s_active[tid] = 0;
-        s_fresh[tid] = 0;
         s_bad[tid] = 0;
         s_load[tid] = 0;
         s_cnt[2 * tid] = 0;
         s_cnt[2 * tid + 1] = 0;
     }
-    __syncthreads();
-    if (tid < NL) {
-        const int slot = s_base + tid;
-        s_frame[tid] = frame_of(A, slot);
-        s_done[tid] = 0;
-        s_round[tid] = 0;
-        s_itsum[tid] = 0;
+    if (epoch && A.resume) {
+        // ---- the lanes this CTA saved at the end of the previous epoch
+        if (tid < NL) {
+            const int32_t* rec = A.lane_save + ((size_t)b * NL + tid) * kLaneRec;
+            s_frame[tid] = (rec[0] >= 0 && rec[0] < A.batch) ? rec[0] : -1;  // a record never saved reads as free
+            s_it[tid] = rec[1];
+            s_round[tid] = min(max(rec[2], 0), A.max_rounds);
+            s_itsum[tid] = rec[3];
+            s_ubest[tid] = rec[4];
+            s_tbest[tid] = rec[5];
+            s_mag[tid] = rec[6];
+            s_ns[tid] = rec[7];
+            s_np[tid] = rec[8];
+            s_done[tid] = 0;
+        }
+        __syncthreads();
+        if (tid < W) {
+            uint32_t valid = 0;
+            for (int l = 0; l < 4; ++l)
+                if (s_frame[4 * tid + l] >= 0) valid |= 0xFFu << (8 * l);
+            s_active[tid] = A.word_save[(size_t)b * 2 * W + tid] & valid;
+            s_fresh[tid] = A.word_save[(size_t)b * 2 * W + W + tid];
+        }
+        __syncthreads();
+        uint32_t was_live = 0;
+#pragma unroll
+        for (int ww = 0; ww < W; ++ww) was_live |= s_active[ww];
+        if (was_live) {  // the soft values and syndrome bits of the lanes in flight
+            const uint32_t* es = A.e_save + (size_t)b * n * W;
+            for (int i = tid; i < n * W; i += T) E_s[i] = es[i];
+            const uint8_t* ss = A.syn_save + (size_t)b * m * W;
+            for (int i = tid; i < m * W; i += T) syn_s[i] = ss[i];
+        }
+        __syncthreads();
+        if (tid == 0) {  // new frames of this launch's list for the free lanes
+            int k = 0;
+            for (int lane = 0; lane < NL; ++lane) k += s_frame[lane] < 0 ? 1 : 0;
+            const int base = k ? atomicAdd(A.queue, k) : 0;
+            int i = 0, any = 0;
+            for (int lane = 0; lane < NL; ++lane) {
+                if (s_frame[lane] >= 0) continue;
+                s_frame[lane] = frame_of(A, base + i++);
+                s_round[lane] = 0;
+                s_itsum[lane] = 0;
+                if (s_frame[lane] >= 0) {
+                    s_load[lane >> 2] |= 0xFFu << (8 * (lane & 3));
+                    any = 1;
+                }
+            }
+            s_any_load = any;
+        }
+    } else {
+        if (tid == 0) s_base = atomicAdd(A.queue, NL);
+        if (tid < W) {
+            s_active[tid] = 0;
+            s_fresh[tid] = 0;
+        }
+        __syncthreads();
+        if (tid < NL) {
+            const int slot = s_base + tid;
+            s_frame[tid] = frame_of(A, slot);
+            s_done[tid] = 0;
+            s_round[tid] = 0;
+            s_itsum[tid] = 0;
+        }
+        __syncthreads();
+        if (tid < W) {
+            uint32_t ld = 0;
+            for (int l = 0; l < 4; ++l)
+                if (s_frame[4 * tid + l] >= 0) ld |= 0xFFu << (8 * l);
+            s_load[tid] = ld;
+        }
+        if (tid == 0) s_any_load = 1;
     }
-    __syncthreads();
-    if (tid < W) {
-        uint32_t ld = 0;
-        for (int l = 0; l < 4; ++l)
-            if (s_frame[4 * tid + l] >= 0) ld |= 0xFFu << (8 * l);
-        s_load[tid] = ld;
-    }
-    if (tid == 0) s_any_load = 1;
+    int cta_iters = 0;  // iterations this CTA has run in this launch
 
     const int* deg = TB.deg;
     const int* off = TB.off;
@@ -210,7 +296,35 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
         uint32_t live = 0;
 #pragma unroll
         for (int ww = 0; ww < W; ++ww) live |= s_active[ww];
-        if (!live) break;
+        if (!live || (epoch && cta_iters >= A.epoch_iters)) {
+            if (epoch) {  // save the lanes for the next epoch (none is pending a write-out or a load here)
+                if (tid < NL) {
+                    int32_t* rec = A.lane_save + ((size_t)b * NL + tid) * kLaneRec;
+                    const int lv = (s_active[tid >> 2] >> (8 * (tid & 3))) & 1u;
+                    rec[0] = lv ? s_frame[tid] : -1;
+                    rec[1] = s_it[tid];
+                    rec[2] = s_round[tid];
+                    rec[3] = s_itsum[tid];
+                    rec[4] = s_ubest[tid];
+                    rec[5] = s_tbest[tid];
+                    rec[6] = s_mag[tid];
+                    rec[7] = s_ns[tid];
+                    rec[8] = s_np[tid];
+                }
+                if (tid < W) {
+                    A.word_save[(size_t)b * 2 * W + tid] = s_active[tid];
+                    A.word_save[(size_t)b * 2 * W + W + tid] = s_fresh[tid];
+                }
+                if (live) {
+                    uint32_t* es = A.e_save + (size_t)b * n * W;
+                    for (int i = tid; i < n * W; i += T) es[i] = E_s[i];
+                    uint8_t* ss = A.syn_save + (size_t)b * m * W;
+                    for (int i = tid; i < m * W; i += T) ss[i] = syn_s[i];
+                }
+            }
+            break;
+        }
+        ++cta_iters;
 
         // ---- one iteration of every active lane
         C.active = s_active[w];
@@ -365,7 +479,7 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
             const int done_f = atomicAdd(A.queue + 1, fin) + fin;
             const unsigned long long done_i = atomicAdd(done_iters, fin_it) + fin_it;
             bool hold = false;
-            if (oldest >= kHoldAfter && done_f >= kHoldMinDone) {
+            if (!epoch && oldest >= kHoldAfter && done_f >= kHoldMinDone) {
                 const long long left = (long long)A.list_len - atomicAdd(A.queue, 0);
                 hold = left <= 0 || 3ull * (unsigned long long)left * done_i <
                                         2ull * (unsigned long long)done_f * gridDim.x * NL * (oldest_end - oldest);
@@ -414,7 +528,7 @@ int launch_p(const ldpc_code* c, const PersistArgs& A, int ctas_per_sm, int thre
     int per_sm = ctas_per_sm > 0 ? (ctas_per_sm < occ ? ctas_per_sm : occ) : occ;
     int64_t grid = (int64_t)sms * per_sm;
     const int64_t need = ((int64_t)A.list_len + 4 * W - 1) / (4 * W);
-    if (grid > need) grid = need;
+    if (grid > need && A.epoch_iters <= 0) grid = need;  // epoch mode keeps its grid: lanes belong to CTAs
     if (grid < 1) grid = 1;
     *grid_out = (int)grid;
     if (dry) return LDPC_OK;

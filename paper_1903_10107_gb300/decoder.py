@@ -220,6 +220,46 @@ class QCCode:
         return bits, iters, ok, rounds
 
 
+    def epoch_state_bytes(self, words: int, ctas_per_sm: int = 0, threads: int = 0):
+        """(bytes, grid) of the lane-state buffer of ``reconcile_epoch`` for a launch shape."""
+        with torch.cuda.device(self.device):
+            return native.ldpc_epoch_state_bytes(self.handle, int(words), int(ctas_per_sm), int(threads))
+
+    def reconcile_epoch(self, bob_bits, llr_mag, syndrome, max_iter: int, lane_state, frame_list, list_len: int,
+                        epoch_iters: int, resume: bool, out, claimed, rank=None, n_short=None, n_punct=None,
+                        known=None, stall_window: int = 0, words: int = 1, ctas_per_sm: int = 0, threads: int = 0):
+        """One epoch of the continuously batched decode (``ldpc_reconcile_epoch``):
+        per-frame arrays indexed by pool slot; ``frame_list[:list_len]`` the
+        slots this epoch may start; ``lane_state`` a uint8 device buffer of
+        ``epoch_state_bytes`` bytes; ``out`` (bits, iters, ok) per slot;
+        ``claimed`` int32[1] receives how many list entries lanes took."""
+        B = bob_bits.shape[0]
+        _dev_ptr(bob_bits, "bob_bits", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(llr_mag, "llr_mag", torch.int8, self.device, (B,))
+        _dev_ptr(syndrome, "syndrome", torch.uint8, self.device, (B, self.mbytes))
+        rp = _dev_ptr(rank, "rank", torch.int32, self.device, (self.n,))
+        sp = _dev_ptr(n_short, "n_short", torch.int32, self.device, (B,))
+        pp = _dev_ptr(n_punct, "n_punct", torch.int32, self.device, (B,))
+        kp = _dev_ptr(known, "known", torch.uint8, self.device, (B, self.nbytes))
+        lp = _dev_ptr(frame_list, "frame_list", torch.int32, self.device)
+        if int(list_len) > frame_list.numel():
+            raise ValueError("list_len exceeds frame_list")
+        _dev_ptr(lane_state, "lane_state", torch.uint8, self.device)
+        bits, iters, ok = out
+        _dev_ptr(bits, "out bits", torch.uint8, self.device, (B, self.nbytes))
+        _dev_ptr(iters, "out iters", torch.int32, self.device, (B,))
+        _dev_ptr(ok, "out ok", torch.uint8, self.device, (B,))
+        _dev_ptr(claimed, "claimed", torch.int32, self.device, (1,))
+        with torch.cuda.device(self.device):
+            native.ldpc_reconcile_epoch(self.handle, bob_bits.data_ptr(), llr_mag.data_ptr(), rp, sp, pp, kp,
+                                        syndrome.data_ptr(), B, lp, int(list_len), int(max_iter), int(stall_window),
+                                        int(epoch_iters), 1 if resume else 0, lane_state.data_ptr(),
+                                        int(lane_state.numel()), int(words), int(ctas_per_sm), int(threads),
+                                        bits.data_ptr(), iters.data_ptr(), ok.data_ptr(), claimed.data_ptr(),
+                                        self._stream())
+        return out
+
+
 def tau_table_device(device=None) -> torch.Tensor:
     """The decoder's byte-lane tau evaluated on the GPU for all (p, q) < 128."""
     device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)

@@ -45,6 +45,9 @@ SIGNATURES = {
                                        _P]),
     "ldpc_reconcile_interactive": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _I, _I, _I, _I, _P,
                                         _P, _P, _P, _P]),
+    "ldpc_epoch_state_bytes": (_I, [_P, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)]),
+    "ldpc_reconcile_epoch": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _I, _I, _P, ctypes.c_size_t,
+                                  _I, _I, _I, _P, _P, _P, _P, _P]),
     "ldpc_code_reserve_persistent": (_I, [_P, _I, _I, _I, _I]),
     "ldpc_relaxed_forward": (_I, [_P, _P, _P, _P, _I, _I, _P, _P, _P, _I, ctypes.c_float, _P, _P, _P, _P]),
     "ldpc_relaxed_backward": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _I, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P,
@@ -160,6 +163,20 @@ def ldpc_reconcile_interactive(code, bob_bits, llr_mag, rank, n_short, n_punct, 
     _call("ldpc_reconcile_interactive", code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome,
           batch, frame_list, list_len, max_iter, stall_window, reveal, max_rounds, words, ctas_per_sm, threads,
           out_bits, out_iters, out_ok, out_rounds, stream)
+
+
+def ldpc_epoch_state_bytes(code, words, ctas_per_sm, threads):
+    b, g = ctypes.c_size_t(), _I()
+    _call("ldpc_epoch_state_bytes", code, words, ctas_per_sm, threads, ctypes.byref(b), ctypes.byref(g))
+    return b.value, g.value
+
+
+def ldpc_reconcile_epoch(code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome, batch, frame_list,
+                         list_len, max_iter, stall_window, epoch_iters, resume, lane_state, lane_state_bytes, words,
+                         ctas_per_sm, threads, out_bits, out_iters, out_ok, out_claimed, stream):
+    _call("ldpc_reconcile_epoch", code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome, batch,
+          frame_list, list_len, max_iter, stall_window, epoch_iters, resume, lane_state, lane_state_bytes, words,
+          ctas_per_sm, threads, out_bits, out_iters, out_ok, out_claimed, stream)
 
 
 def ldpc_code_reserve_persistent(code, list_len, words, ctas_per_sm, threads=0):

@@ -1,4 +1,4 @@
-"""Reconciliation serving loop with continuous batching.
+"""Reconciliation serving loop: continuous batching with resident decoder state.
 
 Requests (one key block each) arrive over time.  Every request is decoded in
 both directions, as in the bi-directional protocol the paper uses (section
@@ -7,34 +7,40 @@ against Bob's; the block is reconciled if either direction recovers the
 other party's key.  Shortened positions hold values both parties know;
 punctured positions are the other party's filler (LLR 0).
 
-Scheduling:
-  * each code has ``slots_per_code`` slots, each with its own code handle
-    (message scratch) and CUDA stream;
-  * arrived requests are admitted while the device has free memory for their
-    buffers (``torch.cuda.mem_get_info`` minus a reserve, and an optional
-    byte budget); the rest wait in arrival order;
-  * whenever a slot is idle, the requests admitted for its code are packed
-    into one persistent launch (two frames per request, hardest first) with
-    their copies in and out on the slot's stream; launches of different
-    slots overlap on the device while new requests keep arriving.
-  * message state stays on the device for all iterations of a launch.
+Each code has one ``EpochEngine``: a device-resident pool of frame slots
+(inputs and outputs, two slots per request), one code handle whose message
+arena holds the lanes' messages, a lane-state buffer, a CUDA stream and
+pinned staging buffers, all allocated once.  The engine runs the persistent
+decoder in epochs (``ldpc_reconcile_epoch``): every epoch runs a bounded
+number of iterations, leaves every unfinished frame's soft values, syndrome
+bits and iteration state in device memory and the messages in the arena,
+and the next epoch continues them while the lanes that came free take the
+requests admitted in between.  So a request that arrives while others are
+decoding joins at the next epoch boundary, its work overlaps theirs on the
+device, and the engines of the different codes overlap on their streams.
 
-Per-request results are deterministic: a block decodes to the same bits
-whether it runs alone or in a mix.
+Admission is by device memory: an engine's pool is sized once from the free
+device memory (minus a reserve, or an explicit byte budget); a request waits
+while its code's pool has no two free slots.
+
+Per-request results are deterministic: a block decodes to the same bits and
+iteration counts whether it runs alone or in a mix, whatever epochs its
+decode is split into.
 """
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import time
-from dataclasses import dataclass, field
+from collections import deque
+from dataclasses import dataclass
 
 import numpy as np
 import torch
 
 from . import inputs, rate
 from .decoder import QCCode, llr_magnitudes
-from .pipeline import hardest_first
 
 
 @dataclass
@@ -54,128 +60,232 @@ class Request:
     bits: tuple = ()        # decoded (bob, alice), packed
 
 
-@dataclass
-class _Slot:
-    code: QCCode
-    stream: torch.cuda.Stream
-    busy: list = field(default_factory=list)
-    event: object = None
-    host_out: tuple = ()
-    nbytes_held: int = 0
-    keep: tuple = ()        # device tensors of the launch in flight
+def pool_bytes_per_frame(nbytes: int, mbytes: int) -> int:
+    """Device bytes of one frame slot: observed key, known values, the other
+    party's key (for the syndrome it sends), syndrome, magnitude, two rate
+    counts, decoded bits, iteration count, flag; plus the staging row."""
+    return 2 * (3 * nbytes + mbytes + 1 + 8) + nbytes + 4 + 1
 
 
-class CodeEntry:
-    def __init__(self, name, base, Z, tiebreak, slots, device):
-        self.name, self.base, self.Z = name, base, Z
-        self.slots = [_Slot(QCCode(base, Z, device), torch.cuda.Stream(device)) for _ in range(slots)]
-        code = self.slots[0].code
-        self.n, self.m, self.nbytes, self.mbytes = code.n, code.m, code.nbytes, code.mbytes
-        self.rank = torch.from_numpy(rate.puncture_rank(base, Z, tiebreak)).to(device)
-        self.queue: list = []
+class EpochEngine:
+    """Continuously batched decoding of one code (see the module docstring)."""
+
+    def __init__(self, name, base, Z, tiebreak, device, capacity: int, llr_scale: float, max_iter: int,
+                 epoch_iters: int = 8, stall_window: int = 0, words: int = 1, ctas_per_sm: int = 1,
+                 threads: int = 0):
+        self.name = name
+        self.device = torch.device(device)
+        self.code = QCCode(base, Z, self.device)
+        c = self.code
+        self.n, self.m, self.nbytes, self.mbytes = c.n, c.m, c.nbytes, c.mbytes
+        self.rank = torch.from_numpy(rate.puncture_rank(base, Z, tiebreak)).to(self.device)
+        self.llr_scale, self.max_iter = float(llr_scale), int(max_iter)
+        self.epoch_iters, self.stall_window = int(epoch_iters), int(stall_window)
+        self.words, self.ctas, self.threads = int(words), int(ctas_per_sm), int(threads)
+        P = 2 * max(1, int(capacity) // 2)
+        self.capacity = P
+        dev = self.device
+        z8 = lambda *sh: torch.zeros(sh, dtype=torch.uint8, device=dev)
+        z32 = lambda *sh: torch.zeros(sh, dtype=torch.int32, device=dev)
+        nb, mb = self.nbytes, self.mbytes
+        # the pool (frame slots) and the same-shaped staging rows of one admission
+        self.obs, self.known, self.syn = z8(P, nb), z8(P, nb), z8(P, mb)
+        self.mag = torch.zeros((P,), dtype=torch.int8, device=dev)
+        self.ns, self.np_ = z32(P), z32(P)
+        self.out = (z8(P, nb), z32(P), z8(P))
+        self.st_obs, self.st_known, self.st_other = z8(P, nb), z8(P, nb), z8(P, nb)
+        self.st_mag = torch.zeros((P,), dtype=torch.int8, device=dev)
+        self.st_ns, self.st_np = z32(P), z32(P)
+        self.d_list, self.d_claimed = z32(P), z32(1)
+        pin8 = lambda *sh: torch.zeros(sh, dtype=torch.uint8).pin_memory()
+        self.h_obs, self.h_known, self.h_other = pin8(P, nb), pin8(P, nb), pin8(P, nb)
+        self.h_mag = torch.zeros((P,), dtype=torch.int8).pin_memory()
+        self.h_ns = torch.zeros((P,), dtype=torch.int32).pin_memory()
+        self.h_np = torch.zeros((P,), dtype=torch.int32).pin_memory()
+        self.h_list = torch.zeros((P,), dtype=torch.int32).pin_memory()
+        self.h_slots = torch.zeros((P,), dtype=torch.int64).pin_memory()
+        self.h_iters = torch.zeros((P,), dtype=torch.int32).pin_memory()
+        self.h_ok = torch.zeros((P,), dtype=torch.uint8).pin_memory()
+        self.h_claimed = torch.zeros((1,), dtype=torch.int32).pin_memory()
+        self.h_rows = torch.zeros((P,), dtype=torch.int64).pin_memory()  # slots of finished frames
+        self.d_rows = torch.zeros((P,), dtype=torch.int64, device=dev)
+        self.d_done_bits = z8(P, nb)
+        self.h_done_bits = pin8(P, nb)
+        state_bytes, self.grid = c.epoch_state_bytes(self.words, self.ctas, self.threads)
+        self.lane_state = z8(state_bytes)
+        self.stream = torch.cuda.Stream(dev)
+        self.free_pairs = deque(range(P // 2))   # request slots: frame slots 2k (Bob) and 2k + 1 (Alice)
+        self.queue: deque = deque()              # requests waiting for admission
+        self.pending: list = []                  # frame slots admitted but not yet taken by a lane
+        self.inflight: dict = {}                 # request slot -> request
+        self.event = None
+        self.started = False
+        self.epochs = 0
+
+    @staticmethod
+    def bytes_for(nbytes: int, mbytes: int, frames: int) -> int:
+        return frames * pool_bytes_per_frame(nbytes, mbytes)
+
+    # ------------------------------------------------------------ admission
+    def admit(self) -> int:
+        """Move waiting requests into free slots: stage their rows in pinned
+        memory, copy them in, compute each direction's syndrome from the other
+        party's key, and place everything in the pool.  Returns how many."""
+        k = min(len(self.queue), len(self.free_pairs))
+        if k == 0:
+            return 0
+        reqs = [self.queue.popleft() for _ in range(k)]
+        pairs = [self.free_pairs.popleft() for _ in range(k)]
+        F = 2 * k
+        q = np.empty(F, np.float64)
+        for i, r in enumerate(reqs):
+            # frame 2i: Bob decodes his key against s_A; 2i + 1: Alice decodes hers against s_B
+            self.h_obs[2 * i].numpy()[:] = r.yb
+            self.h_obs[2 * i + 1].numpy()[:] = r.xa
+            self.h_other[2 * i].numpy()[:] = r.xa
+            self.h_other[2 * i + 1].numpy()[:] = r.yb
+            self.h_known[2 * i].numpy()[:] = r.xa
+            self.h_known[2 * i + 1].numpy()[:] = r.xa
+            q[2 * i] = q[2 * i + 1] = r.qber
+            self.h_ns[2 * i] = self.h_ns[2 * i + 1] = r.n_short
+            self.h_np[2 * i] = self.h_np[2 * i + 1] = r.n_punct
+        self.h_mag[:F] = torch.from_numpy(llr_magnitudes(q, self.llr_scale))
+        slots = np.empty(F, np.int64)
+        slots[0::2] = 2 * np.asarray(pairs)
+        slots[1::2] = 2 * np.asarray(pairs) + 1
+        self.h_slots[:F] = torch.from_numpy(slots)
+        with torch.cuda.stream(self.stream):
+            for d, h in ((self.st_obs, self.h_obs), (self.st_known, self.h_known), (self.st_other, self.h_other),
+                         (self.st_mag, self.h_mag), (self.st_ns, self.h_ns), (self.st_np, self.h_np)):
+                d[:F].copy_(h[:F], non_blocking=True)
+            d_slots = self.h_slots[:F].to(self.device, non_blocking=True)
+            st_syn = self.code.syndrome(self.st_other[:F])  # the syndrome each side receives from the other
+            for pool, st in ((self.obs, self.st_obs), (self.known, self.st_known), (self.mag, self.st_mag),
+                             (self.ns, self.st_ns), (self.np_, self.st_np)):
+                pool.index_copy_(0, d_slots, st[:F])
+            self.syn.index_copy_(0, d_slots, st_syn)
+            self.out[1].index_fill_(0, d_slots, 0)  # iterations 0 = not finished
+        for r, p in zip(reqs, pairs):
+            self.inflight[p] = r
+        self.pending.extend(slots.tolist())
+        return k
+
+    # ------------------------------------------------------------ epochs
+    def launch(self) -> bool:
+        """Start the next epoch if any frame is waiting or in flight."""
+        if self.event is not None or not self.inflight:
+            return False
+        L = len(self.pending)
+        if L:
+            self.h_list[:L] = torch.tensor(self.pending, dtype=torch.int32)
+        with torch.cuda.stream(self.stream):
+            if L:
+                self.d_list[:L].copy_(self.h_list[:L], non_blocking=True)
+            self.code.reconcile_epoch(self.obs, self.mag, self.syn, self.max_iter, self.lane_state, self.d_list, L,
+                                      self.epoch_iters, self.started, self.out, self.d_claimed, rank=self.rank,
+                                      n_short=self.ns, n_punct=self.np_, known=self.known,
+                                      stall_window=self.stall_window, words=self.words, ctas_per_sm=self.ctas,
+                                      threads=self.threads)
+            self.h_iters.copy_(self.out[1], non_blocking=True)
+            self.h_ok.copy_(self.out[2], non_blocking=True)
+            self.h_claimed.copy_(self.d_claimed, non_blocking=True)
+            self.event = torch.cuda.Event()
+            self.event.record(self.stream)
+        self.started = True
+        self.epochs += 1
+        self._launched = L
+        return True
+
+    def poll(self, now: float) -> list:
+        """If the epoch in flight has ended: the requests it completed (their
+        results filled in), after freeing their slots.  Else []."""
+        if self.event is None or not self.event.query():
+            return []
+        self.event = None
+        taken = min(int(self.h_claimed[0]), self._launched)
+        self.pending = self.pending[taken:]  # the rest were not reached: next epoch
+        iters, ok = self.h_iters.numpy(), self.h_ok.numpy()
+        done = [p for p in self.inflight if iters[2 * p] > 0 and iters[2 * p + 1] > 0]
+        if not done:
+            return []
+        R = 2 * len(done)
+        self.h_rows[:R] = torch.from_numpy(np.array([s for p in done for s in (2 * p, 2 * p + 1)], np.int64))
+        with torch.cuda.stream(self.stream):  # the finished frames' bits, gathered into one copy out
+            self.d_rows[:R].copy_(self.h_rows[:R], non_blocking=True)
+            torch.index_select(self.out[0], 0, self.d_rows[:R], out=self.d_done_bits[:R])
+            self.h_done_bits[:R].copy_(self.d_done_bits[:R], non_blocking=True)
+            self.stream.synchronize()
+        bits = self.h_done_bits.numpy()
+        out = []
+        for i, p in enumerate(done):
+            r = self.inflight.pop(p)
+            b0, b1 = bits[2 * i].copy(), bits[2 * i + 1].copy()
+            good = (bool(ok[2 * p]) and np.array_equal(b0, r.xa), bool(ok[2 * p + 1]) and np.array_equal(b1, r.yb))
+            r.ok = good[0] or good[1]
+            r.key_bits = r.n - r.n_punct - r.n_short
+            r.dirs = (good[0], good[1], int(iters[2 * p]), int(iters[2 * p + 1]))
+            r.bits = (b0, b1)
+            r.t_done = now
+            self.free_pairs.append(p)
+            out.append(r)
+        return out
+
+    def idle(self) -> bool:
+        return self.event is None and not self.inflight and not self.queue
 
 
 class ReconciliationServer:
-    def __init__(self, codes, llr_scale: float, max_iter: int, slots_per_code: int = 2, max_batch: int = 512,
-                 mem_budget: int = 0, reserve: int = 512 << 20, device=None):
-        """codes: {name: (base, Z, tiebreak)}."""
+    def __init__(self, codes, llr_scale: float, max_iter: int, epoch_iters: int = 8, stall_window: int = 0,
+                 capacity: int = 1024, mem_budget: int = 0, reserve: int = 1 << 30, ctas_per_sm: int = 1,
+                 max_epoch_iters: int = 64, device=None):
+        """codes: {name: (base, Z, tiebreak)}.  Every code's engine gets a pool
+        of up to ``capacity`` frames, fewer if the free device memory minus
+        ``reserve`` (or ``mem_budget`` bytes, split over the codes) holds
+        fewer; requests beyond the pools wait for admission.  The code with
+        the most edges runs ``epoch_iters`` iterations per epoch, the others
+        as many more as their iterations are cheaper (the same edge updates
+        per epoch), at most ``max_epoch_iters``: an epoch then lasts about as
+        long on every code, and a short code's long decodes are not cut into
+        many epochs whose host round trips would dominate their latency."""
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        self.codes = {name: CodeEntry(name, b, Z, tb, slots_per_code, self.device) for name, (b, Z, tb) in codes.items()}
-        self.by_n = {e.n: e for e in self.codes.values()}
-        self.llr_scale, self.max_iter, self.max_batch = float(llr_scale), int(max_iter), int(max_batch)
-        self.mem_budget, self.reserve = int(mem_budget), int(reserve)
-        self.held = 0
-
-    # ------------------------------------------------------------ memory
-    def _need(self, e: CodeEntry, k: int) -> int:
-        """Device bytes for the buffers of k requests (2 frames each): keys,
-        shortened values, syndromes, per-frame parameters, outputs.  The
-        message scratch belongs to the slot's code handle and is reserved once
-        (at warm-up), not per request."""
-        frames = 2 * k
-        return frames * (4 * e.nbytes + 2 * e.mbytes + 8 + 4 + 4 + 4 + 4 + 1)
-
-    def _admissible(self, e: CodeEntry, k: int) -> bool:
-        need = self._need(e, k)
-        if self.mem_budget and self.held + need > self.mem_budget:
-            return False
         free, _ = torch.cuda.mem_get_info(self.device)
-        return free - self.reserve >= need
+        budget = (free - int(reserve)) if not mem_budget else int(mem_budget)
+        share = max(0, budget) // max(1, len(codes))
+        edges = {name: int((np.asarray(b) >= 0).sum()) * Z for name, (b, Z, tb) in codes.items()}
+        e_max = max(edges.values())
+        self.engines = {}
+        for name, (b, Z, tb) in codes.items():
+            Mb, Nb = np.asarray(b).shape
+            iters = int(min(max_epoch_iters, max(1, round(epoch_iters * e_max / max(1, edges[name])))))
+            nb, mb = (Nb * Z + 7) // 8, (Mb * Z + 7) // 8
+            frames = min(int(capacity), share // pool_bytes_per_frame(nb, mb))
+            if frames < 2:
+                raise RuntimeError(f"serving: the device memory left for code {name} holds no request "
+                                   f"({share} bytes, {2 * pool_bytes_per_frame(nb, mb)} needed)")
+            self.engines[name] = EpochEngine(name, b, Z, tb, self.device, frames, llr_scale, max_iter,
+                                             epoch_iters=iters, stall_window=stall_window,
+                                             ctas_per_sm=ctas_per_sm)
+        self.by_n = {e.n: e for e in self.engines.values()}
 
-    # ------------------------------------------------------------ launch
-    def _launch(self, e: CodeEntry, slot: _Slot, reqs):
-        dev = self.device
-        k = len(reqs)
-        B = 2 * k  # frame 2i: Bob decodes (target s_A); 2i+1: Alice decodes (target s_B)
-        with torch.cuda.stream(slot.stream):
-            obs = np.empty((B, e.nbytes), np.uint8)
-            truth_other = np.empty((B, e.nbytes), np.uint8)
-            known = np.empty((B, e.nbytes), np.uint8)
-            q = np.empty(B, np.float64)
-            npn = np.empty(B, np.int32)
-            nsh = np.empty(B, np.int32)
-            for i, r in enumerate(reqs):
-                obs[2 * i], obs[2 * i + 1] = r.yb, r.xa
-                truth_other[2 * i], truth_other[2 * i + 1] = r.xa, r.yb
-                known[2 * i] = known[2 * i + 1] = r.xa
-                q[2 * i] = q[2 * i + 1] = r.qber
-                npn[2 * i] = npn[2 * i + 1] = r.n_punct
-                nsh[2 * i] = nsh[2 * i + 1] = r.n_short
-            pin = lambda a: torch.from_numpy(a).pin_memory()
-            d_obs = pin(obs).to(dev, non_blocking=True)
-            d_other = pin(truth_other).to(dev, non_blocking=True)  # the other party's key, for its syndrome
-            d_known = pin(known).to(dev, non_blocking=True)
-            d_mag = pin(llr_magnitudes(q, self.llr_scale)).to(dev, non_blocking=True)
-            d_np = pin(npn).to(dev, non_blocking=True)
-            d_ns = pin(nsh).to(dev, non_blocking=True)
-            order = torch.from_numpy(hardest_first(npn, nsh, q)).pin_memory().to(dev, non_blocking=True)
-            syn = slot.code.syndrome(d_other)  # the syndrome each side receives from the other
-            bits, iters, ok = slot.code.reconcile_persistent(d_obs, d_mag, syn, self.max_iter, rank=e.rank,
-                                                             n_short=d_ns, n_punct=d_np, known=d_known,
-                                                             frame_list=order)
-            h_bits = torch.empty(bits.shape, dtype=torch.uint8, pin_memory=True)
-            h_iters = torch.empty(iters.shape, dtype=torch.int32, pin_memory=True)
-            h_ok = torch.empty(ok.shape, dtype=torch.uint8, pin_memory=True)
-            h_bits.copy_(bits, non_blocking=True)
-            h_iters.copy_(iters, non_blocking=True)
-            h_ok.copy_(ok, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(slot.stream)
-            # keep device tensors alive until the launch completes
-            slot.keep = (d_obs, d_other, d_known, d_mag, d_np, d_ns, order, syn, bits, iters, ok)
-        slot.busy, slot.event, slot.host_out = list(reqs), ev, (h_bits, h_iters, h_ok, truth_other)
-        slot.nbytes_held = self._need(e, k)
-        self.held += slot.nbytes_held
-
-    def _finish(self, e: CodeEntry, slot: _Slot, now: float):
-        h_bits, h_iters, h_ok, truth = slot.host_out
-        bits, iters, ok = h_bits.numpy(), h_iters.numpy(), h_ok.numpy()
-        n = e.n
-        for i, r in enumerate(slot.busy):
-            res = []
-            for d in (0, 1):
-                f = 2 * i + d
-                good = bool(ok[f]) and np.array_equal(bits[f], truth[f])
-                res.append(good)
-            r.ok = res[0] or res[1]
-            r.key_bits = n - r.n_punct - r.n_short
-            r.dirs = (res[0], res[1], int(iters[2 * i]), int(iters[2 * i + 1]))
-            r.bits = (bits[2 * i].copy(), bits[2 * i + 1].copy())
-            r.t_done = now
-        self.held -= slot.nbytes_held
-        slot.busy, slot.event, slot.host_out, slot.keep = [], None, (), ()
-
-    # ------------------------------------------------------------ loop
     def serve(self, requests, realtime: bool = True):
         """Serve requests (sorted by t_arrival, seconds from start).  Returns
         the requests with their results and completion times."""
         pending = list(requests)
+        gc_was_on = gc.isenabled()
+        gc.disable()  # a cyclic collection in the loop would stall every request in flight
+        try:
+            self._loop(pending, realtime)
+        finally:
+            if gc_was_on:
+                gc.enable()
+        torch.cuda.synchronize(self.device)
+        return pending
+
+    def _loop(self, pending, realtime):
         t0 = time.perf_counter()
         nxt = 0
-        inflight = 0
-        while nxt < len(pending) or inflight or any(e.queue for e in self.codes.values()):
+        while nxt < len(pending) or not all(e.idle() for e in self.engines.values()):
             now = time.perf_counter() - t0
-            # arrivals
             while nxt < len(pending) and (not realtime or pending[nxt].t_arrival <= now):
                 r = pending[nxt]
                 if not realtime:
@@ -183,38 +293,16 @@ class ReconciliationServer:
                 self.by_n[r.n].queue.append(r)
                 nxt += 1
             progressed = False
-            # completions
-            for e in self.codes.values():
-                for s in e.slots:
-                    if s.event is not None and s.event.query():
-                        self._finish(e, s, time.perf_counter() - t0)
-                        inflight -= 1
+            for e in self.engines.values():
+                if e.poll(time.perf_counter() - t0):
+                    progressed = True
+                if e.event is None:
+                    if e.admit():
                         progressed = True
-            # launches: admitted requests of a code go to its idle slots
-            for e in self.codes.values():
-                for s in e.slots:
-                    if s.event is None and e.queue:
-                        k = min(len(e.queue), self.max_batch)
-                        while k > 0 and not self._admissible(e, k):
-                            k //= 2
-                        if k == 0:
-                            continue
-                        batch, e.queue = e.queue[:k], e.queue[k:]
-                        self._launch(e, s, batch)
-                        inflight += 1
+                    if e.launch():
                         progressed = True
             if not progressed:
-                if inflight == 0:
-                    for e in self.codes.values():
-                        if e.queue and not self._admissible(e, 1):
-                            # nothing in flight will free memory: this request can never start
-                            raise RuntimeError(
-                                f"serving: a request of code {e.name} needs {self._need(e, 1)} device bytes; "
-                                f"the budget ({self.mem_budget or 'none'}) or free memory minus the reserve "
-                                f"({self.reserve}) is smaller")
-                time.sleep(0.0002)
-        torch.cuda.synchronize(self.device)
-        return pending
+                time.sleep(0.00005)
 
 
 # ---------------------------------------------------------------- workload
@@ -279,21 +367,35 @@ def main(argv=None):
     ap.add_argument("--duration", type=float, default=3.0)
     ap.add_argument("--f", type=float, default=1.7)
     ap.add_argument("--max-iter", type=int, default=200)
-    ap.add_argument("--slots", type=int, default=2)
+    ap.add_argument("--epoch-iters", type=int, default=8, help="iterations per epoch of the largest code")
+    ap.add_argument("--stall-window", type=int, default=0)
+    ap.add_argument("--capacity", type=int, default=1024, help="frame slots per code (two per request)")
+    ap.add_argument("--out", default="", help="append the JSON line to this file")
     args = ap.parse_args(argv)
     codes = make_codes()
     count = int(args.rate * args.duration)
     reqs = make_requests(count, args.rate, args.f, codes=codes)
-    srv = ReconciliationServer(codes, llr_scale=1 / 0.29, max_iter=args.max_iter, slots_per_code=args.slots)
+    srv = ReconciliationServer(codes, llr_scale=1 / 0.29, max_iter=args.max_iter, epoch_iters=args.epoch_iters,
+                               stall_window=args.stall_window, capacity=args.capacity)
     srv.serve(make_requests(64, 1e9, args.f, seed=99, codes=codes), realtime=False)  # warm-up
+    epochs0 = {k: e.epochs for k, e in srv.engines.items()}
     t0 = time.perf_counter()
     srv.serve(reqs, realtime=True)
     wall = time.perf_counter() - t0
-    out = {"offered_rate_per_s": args.rate, "duration_s": args.duration, "f_target": args.f, "max_iter": args.max_iter,
-           "slots_per_code": args.slots, "wall_s": wall, **summarize(reqs, wall)}
+    out = {"command": "python -m paper_1903_10107_gb300.serving " + " ".join(argv or []),
+           "offered_rate_per_s": args.rate, "duration_s": args.duration, "f_target": args.f,
+           "max_iter": args.max_iter, "epoch_iters": {k: e.epoch_iters for k, e in srv.engines.items()},
+           "stall_window": args.stall_window,
+           "capacity_frames": {k: e.capacity for k, e in srv.engines.items()},
+           "epochs": {k: e.epochs - epochs0[k] for k, e in srv.engines.items()},
+           "wall_s": wall, **summarize(reqs, wall)}
     print(json.dumps(out), flush=True)
+    if args.out:
+        with open(args.out, "a") as fh:
+            fh.write(json.dumps(out) + "\n")
     return out
 
 
 if __name__ == "__main__":
-    main()
+    import sys
+    main(sys.argv[1:])
