@@ -77,6 +77,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-order", action="store_true", help="persistent launch takes frames in index order")
     ap.add_argument("--separate-rounds", action="store_true",
                     help="interactive: one launch per round (host reads the flags between rounds)")
+    ap.add_argument("--launch", default="", metavar="W,C,T",
+                    help="launch shape words,ctas_per_sm,threads instead of the autotuner's (profiling runs)")
     return ap.parse_args(argv)
 
 
@@ -401,7 +403,9 @@ def fixed_rate_run(args, w, bt, rec, dv, dev, steps, warmup, flush_buf=None):
     stream = torch.cuda.current_stream(dev)
     if w.mixed_rate:
         order = None if args.no_order else hardest_first(bt.n_punct, bt.n_short, bt.q)
-        mrb = MixedRateBatch(rec, w.max_iter, tune_tag="fixed").bind(
+        shape = [int(x) for x in args.launch.split(",")] if args.launch else [0, 0, 0]
+        mrb = MixedRateBatch(rec, w.max_iter, tune_tag="fixed", tune=not args.launch, words=shape[0],
+                             ctas_per_sm=shape[1], threads=shape[2]).bind(
             dv["yb"], dv["syn"], dv["mag"], dv["np"], dv["ns"], dv["xa"], order=order)
         out, step = mrb.out, mrb.run
         kernel = "persistent_kernel"
@@ -521,7 +525,11 @@ def run_ours(args, rank, world, dist):
     if inter:
         proto = InteractiveProtocol(rec, w.max_iter, f_start=args.f_start, df=args.df, max_rounds=args.max_rounds,
                                     stall_window=args.stall_window, fused=not args.separate_rounds)
-        words, ctas, threads = proto.tune(dv["yb"], dv["syn"], bt.q, c(bt.xa))
+        if args.launch:
+            words, ctas, threads = (int(x) for x in args.launch.split(","))
+            proto.words, proto.ctas, proto.threads = words, ctas, threads
+        else:
+            words, ctas, threads = proto.tune(dv["yb"], dv["syn"], bt.q, c(bt.xa))
         d_known = c(bt.xa)
         for _ in range(args.warmup):
             proto.run(dv["yb"], dv["syn"], bt.q, d_known)
