@@ -23,13 +23,14 @@ int launch(const ldpc_code* c, const DecodeArgs& A, int groups, int W, bool tabl
     }
 }
 
-int pick_words(const ldpc_code* c, int batch, int smem_limit, int sms) {
-    for (int W = 4; W >= 2; W >>= 1) {
-        const int64_t groups = (batch + 4 * W - 1) / (4 * W);
-        if ((int64_t)smem_bytes(c, W) <= smem_limit && groups >= 2 * sms) return W;
-    }
-    return 1;
-}
+// One word (4 frames) per CTA: a group holds its SM until the slowest of its
+// frames stops, so the smallest group wins whenever iteration counts are
+// uneven -- n = 4096, 16384 frames at QBER 2 % (max 50): 5.45 ms at one word
+// against 6.88 at two and 9.32 at four (the several-words-per-thread kernel),
+// 8.26 and 12.07 with one word per thread at two and four -- and loses at
+// most 4 % when every frame runs to the cap (QBER 3.5 %, 20 iterations: 4.70
+// against 4.53 and 4.48).  ldpc_decode_batch_words takes 2 or 4 explicitly.
+int pick_words(const ldpc_code*, int, int, int) { return 1; }
 
 int decode_common(const ldpc_code* c, const int8_t* llr, const uint8_t* syn, int batch, int max_iter,
                   const uint8_t* sq, const int8_t* oq, uint8_t* bits, int32_t* iters, uint8_t* ok,

@@ -268,3 +268,24 @@ def test_decode_odd_code_length(Z, Nb):
     for words in (1, 0):
         g, o = _decode_both(base, Z, llr, syn_u, 20, words=words)
         _assert_same(g, o)
+
+
+@pytest.mark.parametrize("dmax", [8, 12, 17, 23, 31])
+@pytest.mark.parametrize("words", [2, 4])
+def test_several_words_per_thread_every_width(dmax, words):
+    """Two or four words (8 or 16 frames) of a row-half in one thread, with
+    8- or 16-byte message and soft-value accesses, at the unroll widths it is
+    used for (up to 16 slots at two words, 9 at four; wider ones take one word
+    per thread), ragged batches, rows of several degrees per code."""
+    Z, Nb = 16, max(dmax, 6)
+    g = np.random.default_rng(300 + dmax)
+    degs = [dmax, max(1, dmax // 2), max(1, (2 * dmax) // 3), 1 + dmax % 3]
+    base = np.full((len(degs), Nb), -1, dtype=np.int32)
+    for i, d in enumerate(degs):
+        cols = g.choice(Nb, size=d, replace=False)
+        base[i, cols] = g.integers(0, Z, size=d)
+    B, q, T = 37, 0.04, 14
+    xa, yb = _frames(base, Z, B, q, 400 + dmax)
+    llr, syn_u = _oracle_inputs(base, Z, xa, yb, q)
+    gg, o = _decode_both(base, Z, llr, syn_u, T, words=words)
+    _assert_same(gg, o)
