@@ -547,7 +547,7 @@ def run_ours(args, rank, world, dist):
         for _ in range(args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res = proto.run(dv["yb"], dv["syn"], bt.q, d_known, timing=True)
+            res = proto.run(dv["yb"], dv["syn"], bt.q, d_known, timing=True, bits_out="device")
             e1.record(stream)
             torch.cuda.synchronize()
             step_times.append(e0.elapsed_time(e1) / 1e3)
@@ -557,7 +557,7 @@ def run_ours(args, rank, world, dist):
         clk = clocks.stop()
         step_s = float(np.mean(step_times))
         dec_s = float(np.mean(kern))
-        got = inputs.unpack_bits(res["bits"], w.n)
+        got = inputs.unpack_bits(res["bits"].cpu().numpy(), w.n)
         corr = res["ok"].astype(bool) & np.all(got == xa_bits, axis=1)
         corr_key, all_key = float(res["key_bits"][corr].sum()), float(res["key_bits"].sum())
         it_sum = float(res["iters"].sum())
@@ -577,7 +577,17 @@ def run_ours(args, rank, world, dist):
                            "peak_kind": "measured in this run: device copy of a 24 MB buffer held in L2"}
         roof = roofline_hbm(alg, dec_s, "persistent_kernel", traffic, extra)
         fer = 1.0 - float(corr.mean())
+        by_qber = []
+        for lo in np.arange(0.01, 0.08, 0.01):
+            sel = (bt.q >= lo) & (bt.q < lo + 0.01)
+            if sel.any():
+                by_qber.append({"qber": [round(float(lo), 2), round(float(lo) + 0.01, 2)], "frames": int(sel.sum()),
+                                "fer": 1.0 - float(corr[sel].mean()), "f_mean": float(res["f"][sel].mean()),
+                                "rounds_mean": float(res["rounds"][sel].mean()),
+                                "iters_mean": float(res["iters"][sel].mean()),
+                                "key_share": float(res["key_bits"][sel & corr].sum()) / max(corr_key, 1.0)})
         extra_keys = {"fer": fer, "efficiency_f_mean": float(res["f"][corr].mean()) if corr.any() else None,
+                      "by_qber": by_qber,
                       "efficiency_f_all_frames": float(res["f"].mean()),
                       "rounds_mean": float(res["rounds"].mean()), "rounds_max": int(res["rounds"].max()),
                       "iters_mean_total": float(res["iters"].mean()),
@@ -592,12 +602,13 @@ def run_ours(args, rank, world, dist):
         if not args.no_e2e:
             pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
             h_yb, h_syn, h_kn = pin(bt.yb), dv["syn"].cpu().pin_memory(), pin(bt.xa)
-            proto.run_host(h_yb, h_syn, bt.q, h_kn)
+            h_bits = torch.empty((B, code.nbytes), dtype=torch.uint8, pin_memory=True)
+            proto.run_host(h_yb, h_syn, bt.q, h_kn, bits_out=h_bits)
             torch.cuda.synchronize()
             e2e_steps = max(2, min(args.steps, 3))
             t0 = time.perf_counter()
             for _ in range(e2e_steps):
-                eres, h2d, d2h = proto.run_host(h_yb, h_syn, bt.q, h_kn)
+                eres, h2d, d2h = proto.run_host(h_yb, h_syn, bt.q, h_kn, bits_out=h_bits)
             torch.cuda.synchronize()
             e2e_s = (time.perf_counter() - t0) / e2e_steps
             ecorr = eres["ok"].astype(bool) & np.all(inputs.unpack_bits(eres["bits"], w.n) == xa_bits, axis=1)

@@ -354,18 +354,42 @@ class InteractiveProtocol:
             res["launches"] = len(events)
         return res
 
-    def run(self, bob, syn, qber_host, known, timing: bool = False):
+    def run(self, bob, syn, qber_host, known, timing: bool = False, bits_out=None):
         """bob, syn, known: device tensors for all frames; qber_host: numpy.
         Returns dict of host arrays: bits, iters (summed over rounds), ok,
         rounds (the last round decoded), revealed, key_bits, f; the
         host<->device bytes of the rounds' control (h2d_bytes, d2h_bytes);
         with ``timing`` also kernel_s (summed device time of the decoder
-        launches) and launches."""
-        if self.fused:
-            return self._run_fused(bob, syn, qber_host, known, timing)
-        return self._run_rounds(bob, syn, qber_host, known, timing)
+        launches) and launches.
 
-    def _run_fused(self, bob, syn, qber_host, known, timing):
+        ``bits_out`` selects where the corrected keys go: None copies them
+        to a new host array; ``"device"`` leaves them on the device
+        (``res["bits"]`` is then the device tensor and d2h_bytes excludes
+        them); a uint8 host tensor of shape (frames, ceil(n/8)), ideally
+        pinned, receives them (``res["bits"]`` is its numpy view, valid
+        until the buffer is reused)."""
+        if self.fused:
+            return self._run_fused(bob, syn, qber_host, known, timing, bits_out)
+        return self._run_rounds(bob, syn, qber_host, known, timing, bits_out)
+
+    @staticmethod
+    def _bits_to(bits, bits_out):
+        """(bits where ``bits_out`` asks, bytes copied to the host)."""
+        if isinstance(bits_out, str):
+            if bits_out != "device":
+                raise ValueError(f"bits_out must be None, 'device' or a host tensor, not {bits_out!r}")
+            return bits, 0
+        if bits_out is None:
+            h = bits.cpu().numpy()
+            return h, h.nbytes
+        if tuple(bits_out.shape) != tuple(bits.shape) or bits_out.dtype != bits.dtype or bits_out.is_cuda:
+            raise ValueError("bits_out must be a host uint8 tensor of shape (frames, ceil(n/8))")
+        bits_out.copy_(bits, non_blocking=bits.is_cuda and bits_out.is_pinned())
+        if bits.is_cuda:
+            torch.cuda.current_stream(bits.device).synchronize()
+        return bits_out.numpy(), int(bits.numel())
+
+    def _run_fused(self, bob, syn, qber_host, known, timing, bits_out=None):
         dev = self.code.device
         q = np.asarray(qber_host, dtype=np.float64)
         B = q.size
@@ -386,12 +410,13 @@ class InteractiveProtocol:
         if timing:
             e1.record(stream)
             events = [(e0, e1)]
-        bits, iters, ok, rounds = (t.cpu().numpy() for t in (bits, iters, ok, rounds))
-        d2h = bits.nbytes + 4 * B + B + 4 * B
+        iters, ok, rounds = (t.cpu().numpy() for t in (iters, ok, rounds))
+        bits, d2h = self._bits_to(bits, bits_out)
+        d2h += 4 * B + B + 4 * B
         revealed = rev[np.arange(B), rounds]
         return self._finish(q, p0, s0, revealed, bits, iters.astype(np.int64), ok, rounds, h2d, d2h, events)
 
-    def _run_rounds(self, bob, syn, qber_host, known, timing: bool = False):
+    def _run_rounds(self, bob, syn, qber_host, known, timing: bool = False, bits_out=None):
         dev = self.code.device
         n, m = self.code.n, self.code.m
         q = np.asarray(qber_host, dtype=np.float64)
@@ -441,21 +466,26 @@ class InteractiveProtocol:
             revealed[todo] += r
             n_short[todo] = (s0[todo] + revealed[todo]).astype(np.int32)
             n_punct[todo] = np.maximum(p0[todo] - revealed[todo], 0).astype(np.int32)
-        bits, _, okd = (t.cpu().numpy() for t in out)
-        d2h += bits.nbytes + 5 * B
+        okd = out[2].cpu().numpy()
+        bits, nb = self._bits_to(out[0], bits_out)
+        d2h += nb + 5 * B
         return self._finish(q, p0, s0, revealed, bits, iters_total, okd, rounds, h2d, d2h,
                             events if timing else None)
 
-    def run_host(self, bob_h, syn_h, qber_host, known_h, timing: bool = False):
+    def run_host(self, bob_h, syn_h, qber_host, known_h, timing: bool = False, bits_out=None):
         """``run`` from host buffers (ideally pinned): Bob's keys, Alice's
         syndromes and the values Alice reveals (her key; only revealed and
         shortened positions are read) are copied to the device, the rounds
-        run, and the final bits, iteration counts and flags come back.
-        Returns (result dict as for ``run``, h2d_bytes, d2h_bytes).  The
-        copies are torch copies issued by this Python layer around the C-ABI
-        launches (the C ABI itself takes device pointers)."""
+        run, and the final bits, iteration counts and flags come back (the
+        bits into ``bits_out`` when given, a host uint8 tensor of shape
+        (frames, ceil(n/8))).  Returns (result dict as for ``run``,
+        h2d_bytes, d2h_bytes).  The copies are torch copies issued by this
+        Python layer around the C-ABI launches (the C ABI itself takes
+        device pointers)."""
+        if isinstance(bits_out, str):
+            raise ValueError("run_host returns the bits to the host: bits_out must be None or a host tensor")
         dev = self.code.device
         d = [t.to(dev, non_blocking=True) for t in (bob_h, syn_h, known_h)]
         h2d = sum(int(t.numel() * t.element_size()) for t in (bob_h, syn_h, known_h))
-        res = self.run(d[0], d[1], qber_host, d[2], timing=timing)
+        res = self.run(d[0], d[1], qber_host, d[2], timing=timing, bits_out=bits_out)
         return res, h2d + res["h2d_bytes"], res["d2h_bytes"]

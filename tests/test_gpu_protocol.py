@@ -76,6 +76,12 @@ def test_interactive_protocol_matches_the_oracle_protocol(stall, fused):
     hres, h2d, d2h = proto.run_host(pin(yb), syn.cpu().pin_memory(), q, pin(xa))
     assert np.array_equal(hres["bits"], res["bits"]) and np.array_equal(hres["iters"], res["iters"])
     assert h2d >= yb.nbytes + syn.numel() + xa.nbytes and d2h >= res["bits"].nbytes + 5 * B
+    # the same bits left on the device, and copied into a caller's pinned buffer
+    dres = proto.run(c(yb), syn, q, c(xa), bits_out="device")
+    assert dres["bits"].is_cuda and np.array_equal(dres["bits"].cpu().numpy(), res["bits"])
+    buf = torch.empty(res["bits"].shape, dtype=torch.uint8, pin_memory=True)
+    bres, _, _ = proto.run_host(pin(yb), syn.cpu().pin_memory(), q, pin(xa), bits_out=buf)
+    assert np.array_equal(buf.numpy(), res["bits"]) and np.array_equal(bres["ok"], res["ok"])
 
 
 def test_host_buffer_path_matches_oracle_and_counts_bytes():

@@ -132,3 +132,45 @@ def test_fused_rounds_take_the_same_reveals_as_separate_rounds():
     np.testing.assert_allclose(sep["f"], fus["f"], rtol=1e-12)
     # every frame's revealed count is the table's entry at its last round
     assert np.array_equal(fus["revealed"], rev[np.arange(B), fus["rounds"]])
+
+
+def test_bits_destinations():
+    """The corrected keys go where ``bits_out`` asks: a new host array by
+    default, left as the decoder's tensor for ``"device"`` (not counted as
+    copied back), or copied into a caller's host buffer; other values are
+    refused."""
+    n, m = 4096, 1024
+    q = np.array([0.02, 0.05, 0.07])
+    B = q.size
+
+    class PatternCode(FakeFusedCode):
+        def reconcile_interactive(self, *a, **k):
+            bits, iters, ok, last = super().reconcile_interactive(*a, **k)
+            bits[:] = torch.arange(B, dtype=torch.uint8)[:, None] + 1
+            self.bits = bits
+            return bits, iters, ok, last
+
+    mk = lambda code: types.SimpleNamespace(code=code, rank=torch.zeros(n, dtype=torch.int32), llr_scale=3.0,
+                                            magnitudes=lambda qq: np.zeros(len(qq), np.int8))
+    args = (torch.zeros((B, n // 8), dtype=torch.uint8), torch.zeros((B, m // 8), dtype=torch.uint8), q,
+            torch.zeros((B, n // 8), dtype=torch.uint8))
+    kw = dict(max_iter=50, f_start=1.1, df=0.1, max_rounds=3)
+    want = np.repeat(np.arange(1, B + 1, dtype=np.uint8)[:, None], n // 8, axis=1)
+    code = PatternCode(n, m, np.array([0, 1, 2]))
+    proto = InteractiveProtocol(mk(code), **kw)
+    plain = proto.run(*args)
+    assert isinstance(plain["bits"], np.ndarray) and np.array_equal(plain["bits"], want)
+    dev = proto.run(*args, bits_out="device")
+    assert dev["bits"] is code.bits
+    assert dev["d2h_bytes"] == plain["d2h_bytes"] - B * (n // 8)
+    buf = torch.zeros((B, n // 8), dtype=torch.uint8)
+    into = proto.run(*args, bits_out=buf)
+    assert np.array_equal(buf.numpy(), want) and np.shares_memory(into["bits"], buf.numpy())
+    assert into["d2h_bytes"] == plain["d2h_bytes"]
+    for bad in ("host", torch.zeros((B, 1), dtype=torch.uint8), torch.zeros((B, n // 8), dtype=torch.int32)):
+        try:
+            proto.run(*args, bits_out=bad)
+        except ValueError:
+            pass
+        else:
+            raise AssertionError(f"bits_out={bad!r} accepted")
