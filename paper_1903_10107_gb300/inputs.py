@@ -24,6 +24,7 @@ import numpy as np
 __all__ = [
     "generator",
     "qc_base_matrix",
+    "peg_base_matrix",
     "mixed_column_degrees",
     "alice_keys",
     "bsc_noise",
@@ -52,6 +53,73 @@ def qc_base_matrix(Mb: int, Nb: int, Z: int, col_degrees, seed: int) -> np.ndarr
         rows = g.choice(Mb, size=int(col_degrees[k]), replace=False)
         shifts = g.integers(0, Z, size=int(col_degrees[k]))
         base[rows, k] = shifts
+    return base
+
+
+def peg_base_matrix(Mb: int, Nb: int, Z: int, col_degrees, seed: int, max_draws: int = 1000) -> np.ndarray:
+    """A base matrix whose mask is grown by progressive edge growth (PEG, Hu,
+    Eleftheriou and Arnold 2005; the paper builds its masks this way,
+    section 4.1) and whose shifts close no 4-cycle in the lifted graph.
+
+    Mask: columns are taken in order of ascending degree (stable).  A
+    column's first edge goes to a row of least current degree; each further
+    edge to a row as far as possible from the column in the graph built so
+    far: a row it cannot reach if there is one, else one of the rows reached
+    last by a breadth-first expansion.  Among those the least-degree rows
+    qualify; one is drawn uniformly.  This keeps the row degrees within one
+    of each other.
+
+    Shifts: edge by edge in the same order, a shift is drawn uniformly from
+    ``[0, Z)`` and drawn again while, with two rows i, i' and two columns j,
+    j' already holding nonzero blocks, ``s(i,j) - s(i',j) + s(i',j') -
+    s(i,j') = 0 (mod Z)`` (the lifted graph would then hold a 4-cycle), so
+    the code's girth is at least 6 like the finite-field codes of section 4.1.
+    Raises if ``max_draws`` draws of one shift all close a 4-cycle."""
+    col_degrees = np.broadcast_to(np.asarray(col_degrees, dtype=np.int64), (Nb,))
+    if np.any(col_degrees > Mb) or np.any(col_degrees < 0):
+        raise ValueError("column degree out of range")
+    g = generator(seed, 7)
+    row_deg = np.zeros(Mb, dtype=np.int64)
+    col_rows = [[] for _ in range(Nb)]
+    row_cols = [[] for _ in range(Mb)]
+    order = np.argsort(col_degrees, kind="stable")
+    for j in order:
+        for k in range(int(col_degrees[j])):
+            if k == 0:
+                pool = np.arange(Mb)
+            else:
+                reached = set(col_rows[j])
+                seen_cols = {int(j)}
+                pool = None
+                while True:
+                    unreached = [i for i in range(Mb) if i not in reached]
+                    if not unreached:
+                        break
+                    pool = unreached
+                    cols = {c for i in reached for c in row_cols[i]} - seen_cols
+                    seen_cols |= cols
+                    new = {i for c in cols for i in col_rows[c]} - reached
+                    if not new:
+                        break
+                    reached |= new
+                pool = np.array(pool, dtype=np.int64)
+            pool = pool[row_deg[pool] == row_deg[pool].min()]
+            i = int(g.choice(pool))
+            col_rows[j].append(i)
+            row_cols[i].append(int(j))
+            row_deg[i] += 1
+    base = np.full((Mb, Nb), -1, dtype=np.int32)
+    for j in order:
+        for i in col_rows[j]:
+            for _ in range(max_draws):
+                s = int(g.integers(0, Z))
+                if not any((s - base[i2, j] + base[i2, j2] - base[i, j2]) % Z == 0
+                           for i2 in col_rows[j] if i2 != i and base[i2, j] >= 0
+                           for j2 in row_cols[i] if j2 != j and base[i, j2] >= 0 and base[i2, j2] >= 0):
+                    break
+            else:
+                raise RuntimeError(f"no 4-cycle-free shift for block ({i}, {j}) in {max_draws} draws")
+            base[i, j] = s
     return base
 
 
@@ -111,7 +179,7 @@ class Workload:
     """Shape and seeds of one synthetic workload (no arithmetic of the method)."""
 
     def __init__(self, name, Mb, Nb, Z, batch, max_iter, qber, col_degrees,
-                 code_seed=1, frame_seed=2, mixed_rate=False, target_f=None, llr_scale=8.0):
+                 code_seed=1, frame_seed=2, mixed_rate=False, target_f=None, llr_scale=8.0, mask="uniform"):
         self.name = name
         self.Mb, self.Nb, self.Z = Mb, Nb, Z
         self.n, self.m = Nb * Z, Mb * Z
@@ -122,12 +190,16 @@ class Workload:
         self.mixed_rate = mixed_rate
         self.target_f = target_f
         self.llr_scale = llr_scale  # channel LLR LSB per nat
+        if mask not in ("uniform", "peg"):
+            raise ValueError("mask must be 'uniform' or 'peg'")
+        self.mask = mask            # base-matrix construction: qc_base_matrix or peg_base_matrix
 
     def base(self) -> np.ndarray:
         degs = self.col_degrees
         if callable(degs):
             degs = degs(self)
-        return qc_base_matrix(self.Mb, self.Nb, self.Z, degs, self.code_seed)
+        make = peg_base_matrix if self.mask == "peg" else qc_base_matrix
+        return make(self.Mb, self.Nb, self.Z, degs, self.code_seed)
 
     def qbers(self, batch=None, first: int = 0) -> np.ndarray:
         """QBER of frames ``first .. first+batch-1``."""
@@ -154,11 +226,12 @@ WORKLOADS = {
     "n4096_r075_q02": Workload("n4096_r075_q02", 8, 32, 128, 64, 50, 0.02, 3),
     # single column-3 code, rate 0.8, 8192 frames at QBER 3 %
     "n40960_r080_q03": Workload("n40960_r080_q03", 16, 80, 512, 8192, 100, 0.03, 3),
-    # 3/6 mixed-degree mother code, per-frame QBER 1-8 %, per-frame rate for a
-    # common efficiency target; LLRs quantised with the step at which the
-    # check-node table represents the box-plus (0.29 nat per LSB)
+    # 3/6 mixed-degree mother code with a PEG mask (row degrees 15 and 16) and
+    # 4-cycle-free shifts, per-frame QBER 1-8 %, per-frame rate for a common
+    # efficiency target; LLRs quantised with the step at which the check-node
+    # table represents the box-plus (0.29 nat per LSB)
     "n49152_mixed_q01_08": Workload("n49152_mixed_q01_08", 24, 96, 512, 16384, 200, (0.01, 0.08),
-                                    _mixed_3_6, mixed_rate=True, target_f=1.7, llr_scale=1 / 0.29),
+                                    _mixed_3_6, mixed_rate=True, target_f=1.7, llr_scale=1 / 0.29, mask="peg"),
     # the n=4096 code at QBER 2-4 %, for the FP32 relaxation
     "n4096_relaxed_q02_04": Workload("n4096_relaxed_q02_04", 8, 32, 128, 1024, 20, (0.02, 0.04), 3),
 }

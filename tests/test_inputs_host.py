@@ -31,6 +31,61 @@ def test_mixed_code_split_and_edges():
     cd = (base >= 0).sum(axis=0)
     assert sorted(set(cd.tolist())) == [3, 6] and (cd == 6).sum() == 29 and (cd == 3).sum() == 67
     assert int((base >= 0).sum()) * w.Z == 192000
+    assert w.mask == "peg" and sorted(set((base >= 0).sum(axis=1).tolist())) == [15, 16]
+    assert inputs.WORKLOADS["n40960_r080_q03"].mask == "uniform" and inputs.WORKLOADS["n4096_r075_q02"].mask == "uniform"
+
+
+def _dense_h(base, Z):
+    Mb, Nb = base.shape
+    H = np.zeros((Mb * Z, Nb * Z), dtype=np.int64)
+    for i in range(Mb):
+        for j in range(Nb):
+            if base[i, j] >= 0:
+                for r in range(Z):
+                    H[i * Z + r, j * Z + (r + base[i, j]) % Z] = 1
+    return H
+
+
+@pytest.mark.parametrize("Mb,Nb,Z,seed", [(6, 24, 64, 1), (4, 12, 16, 3), (24, 96, 512, 1)])
+def test_peg_mask_degrees_and_girth(Mb, Nb, Z, seed):
+    """PEG masks: the column degrees asked for, row degrees within one of
+    each other, and a lifted graph without 4-cycles (no two rows of H share
+    two columns: H H^T has no off-diagonal entry above 1), checked on the
+    expanded matrix itself."""
+    import scipy.sparse as sp
+    degs = inputs.mixed_column_degrees(Nb, 0.3, 2 if Mb < 6 else 3, 4 if Mb < 6 else 6, seed)
+    base = inputs.peg_base_matrix(Mb, Nb, Z, degs, seed)
+    assert np.array_equal((base >= 0).sum(axis=0), degs)
+    rd = (base >= 0).sum(axis=1)
+    assert rd.max() - rd.min() <= 1
+    assert base[base >= 0].min() >= 0 and base.max() < Z
+    assert np.array_equal(base, inputs.peg_base_matrix(Mb, Nb, Z, degs, seed))  # seeded
+    if Mb * Z <= 400:
+        HH = _dense_h(base, Z) @ _dense_h(base, Z).T
+    else:
+        rows, cols = [], []
+        for i, j in zip(*np.nonzero(base >= 0)):
+            r = np.arange(Z)
+            rows.append(i * Z + r)
+            cols.append(j * Z + (r + base[i, j]) % Z)
+        rows, cols = np.concatenate(rows), np.concatenate(cols)
+        H = sp.csr_matrix((np.ones(rows.size, np.int64), (rows, cols)), shape=(Mb * Z, Nb * Z))
+        HH = (H @ H.T).tocoo()
+    if sp.issparse(HH):
+        off = HH.row != HH.col
+        assert HH.data[off].max() <= 1
+    else:
+        np.fill_diagonal(HH, 0)
+        assert HH.max() <= 1
+
+
+def test_uniform_draw_has_four_cycles_somewhere():
+    """The 4-cycle check above can fail: a uniform draw of the small code
+    with few shift values holds 4-cycles."""
+    base = inputs.qc_base_matrix(6, 24, 4, 3, 1)
+    HH = _dense_h(base, 4) @ _dense_h(base, 4).T
+    np.fill_diagonal(HH, 0)
+    assert HH.max() >= 2
 
 
 def test_workload_shapes():
