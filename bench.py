@@ -653,9 +653,12 @@ def run_ours(args, rank, world, dist):
                                      torch.cuda.get_device_properties(dev).multi_processor_count),
         "e2e": {"value": e_tot / e2e_max / 1e6 if e2e is not None else None, "unit": "Mbps",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "path": ("InteractiveProtocol.run_host" if inter else "Reconciler.reconcile_host_stream") +
-                        ": torch copies from pinned host buffers, issued by the Python layer around the C-ABI "
-                        "launches (the C ABI takes device pointers)"},
+                "path": ("the C-ABI host-buffer call ldpc_reconcile_interactive_host (via InteractiveProtocol."
+                         "run_host): pinned host buffers in and out, the library's own copies around its one "
+                         "launch" if inter and not args.separate_rounds else
+                         ("InteractiveProtocol.run_host" if inter else "Reconciler.reconcile_host_stream") +
+                         ": torch copies from pinned host buffers, issued by the Python layer around the C-ABI "
+                         "launches (the C ABI takes device pointers)")},
         "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
         "paper_context": "60 Mbps at f~1.1 on an Intel i7-6700HQ (section 4.2, Table 2), other codes and hardware",
     }

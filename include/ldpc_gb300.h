@@ -222,6 +222,36 @@ int ldpc_reconcile_interactive(const ldpc_code* code, const uint8_t* bob_bits, c
                                uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, int32_t* out_rounds,
                                void* stream);
 
+/* ldpc_reconcile_interactive from host buffers, for callers whose frames
+ * and results live in host memory (the end-to-end form of the protocol of
+ * sections 4.1 and 4.2): every input is copied into device buffers that the
+ * code handle owns, the one persistent launch runs, and the outputs are
+ * copied back; the call returns once they are in host memory (it
+ * synchronises `stream`).
+ *   Every pointer argument is host memory with the layout and meaning of the
+ *   same argument of ldpc_reconcile_interactive, rank included (int32[n],
+ *   copied on every call).  Page-locked memory (cudaHostAlloc, or torch's
+ *   pin_memory) makes the copies asynchronous DMA; pageable memory works,
+ *   the driver then stages it.
+ *   Outputs of frames that frame_list does not contain keep the values the
+ *   caller's buffers held (they are copied in first when the list does not
+ *   cover every frame).
+ *   h2d_bytes, d2h_bytes : host, int64[1] each, or NULL: the bytes this call
+ *   copied to and from the device.
+ * The device copies are cached on the handle and grow on demand (cudaMalloc
+ * when a call needs more than an earlier one), so the call is not for CUDA
+ * graph capture, and two calls on one handle must not run concurrently
+ * (from two host threads) -- they share the copies.  Errors as for
+ * ldpc_reconcile_interactive; LDPC_ENOMEM if the copies cannot be
+ * allocated. */
+int ldpc_reconcile_interactive_host(const ldpc_code* code, const uint8_t* bob_bits, const int8_t* llr_mag,
+                                    const int32_t* rank, const int32_t* n_short, const int32_t* n_punct,
+                                    const uint8_t* known, const uint8_t* target_syndrome, int batch,
+                                    const int32_t* frame_list, int list_len, int max_iter, int stall_window,
+                                    const int32_t* reveal, int max_rounds, int words, int ctas_per_sm, int threads,
+                                    uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, int32_t* out_rounds,
+                                    int64_t* h2d_bytes, int64_t* d2h_bytes, void* stream);
+
 /* Bytes of the lane-state buffer that ldpc_reconcile_epoch needs for a launch
  * shape (words 1, 2 or 4 explicitly; ctas_per_sm and threads as in
  * ldpc_reconcile_persistent), and the grid that shape runs (`grid` may be

@@ -48,6 +48,24 @@ int ensure_arena(ldpc_code* c, size_t bytes) {
     return LDPC_OK;
 }
 
+int ensure_io(ldpc_code* c, size_t bytes) {
+    if (bytes <= c->io_bytes) return LDPC_OK;
+    if (c->io) {
+        LDPC_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(c->io);
+        c->io = nullptr;
+        c->io_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->io, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LDPC_ENOMEM, std::string("host-buffer staging of ") + std::to_string(bytes) + " bytes: " +
+                                     cudaGetErrorString(e));
+    }
+    c->io_bytes = bytes;
+    return LDPC_OK;
+}
+
 }  // namespace ldpc
 
 extern "C" {
@@ -109,6 +127,7 @@ void ldpc_code_destroy(ldpc_code* c) {
     cudaDeviceSynchronize();
     if (c->d_tab) cudaFree(c->d_tab);
     if (c->arena) cudaFree(c->arena);
+    if (c->io) cudaFree(c->io);
     if (c->d_queue) cudaFree(c->d_queue);
     delete c;
 }

@@ -24,6 +24,8 @@ struct ldpc_code {
     size_t tab_words = 0;
     void* arena = nullptr;  // message scratch
     size_t arena_bytes = 0;
+    void* io = nullptr;     // device copies of the host-buffer entry points' inputs and outputs
+    size_t io_bytes = 0;
     int* d_queue = nullptr; // work counter of the persistent decoder
 };
 
@@ -34,6 +36,7 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 void count_launch(int64_t k = 1);
 int ensure_arena(ldpc_code* c, size_t bytes);
+int ensure_io(ldpc_code* c, size_t bytes);
 int max_dyn_smem(int device);
 
 inline const int32_t* tab_deg(const int32_t* t) { return t; }

@@ -7,6 +7,8 @@ CUDA stream.  Every computation runs in the library's CUDA kernels.
 """
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 import torch
 
@@ -18,6 +20,23 @@ def _dev_ptr(t: torch.Tensor | None, name: str, dtype, device, shape=None) -> in
         return None
     if not t.is_cuda or t.device != device:
         raise ValueError(f"{name} must be a CUDA tensor on {device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _host_ptr(t, name: str, dtype, shape=None) -> int:
+    """Address of a contiguous host tensor (ideally pinned) or numpy array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        t = torch.from_numpy(t)
+    if t.is_cuda:
+        raise ValueError(f"{name} must be in host memory")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -218,6 +237,43 @@ class QCCode:
                                               bits.data_ptr(), iters.data_ptr(), ok.data_ptr(), rounds.data_ptr(),
                                               self._stream())
         return bits, iters, ok, rounds
+
+    def reconcile_interactive_host(self, bob_bits, llr_mag, syndrome, max_iter: int, rank, n_short, n_punct, known,
+                                   reveal, frame_list=None, stall_window: int = 0, words: int = 0,
+                                   ctas_per_sm: int = 0, threads: int = 0, out=None):
+        """``reconcile_interactive`` from host buffers
+        (``ldpc_reconcile_interactive_host``): every argument a contiguous
+        host tensor or numpy array (pinned memory copies asynchronously), the
+        copies to and from the device made by the library.  ``out``: host
+        ``(bits, iters, ok, rounds)`` tensors, or None for new ones.
+        Returns ``(bits, iters, ok, rounds, h2d_bytes, d2h_bytes)``."""
+        B = int(bob_bits.shape[0])
+        R = int(reveal.shape[1]) - 1
+        args = [_host_ptr(bob_bits, "bob_bits", torch.uint8, (B, self.nbytes)),
+                _host_ptr(llr_mag, "llr_mag", torch.int8, (B,)),
+                _host_ptr(rank, "rank", torch.int32, (self.n,)),
+                _host_ptr(n_short, "n_short", torch.int32, (B,)),
+                _host_ptr(n_punct, "n_punct", torch.int32, (B,)),
+                _host_ptr(known, "known", torch.uint8, (B, self.nbytes)),
+                _host_ptr(syndrome, "syndrome", torch.uint8, (B, self.mbytes))]
+        rv = _host_ptr(reveal, "reveal", torch.int32, (B, R + 1))
+        if frame_list is not None:
+            lp, nl = _host_ptr(frame_list, "frame_list", torch.int32), int(frame_list.shape[0])
+        else:
+            lp, nl = None, B
+        if out is None:
+            out = (torch.zeros((B, self.nbytes), dtype=torch.uint8), torch.zeros((B,), dtype=torch.int32),
+                   torch.zeros((B,), dtype=torch.uint8), torch.zeros((B,), dtype=torch.int32))
+        bits, iters, ok, rounds = out
+        op = [_host_ptr(bits, "out bits", torch.uint8, (B, self.nbytes)),
+              _host_ptr(iters, "out iters", torch.int32, (B,)), _host_ptr(ok, "out ok", torch.uint8, (B,)),
+              _host_ptr(rounds, "out rounds", torch.int32, (B,))]
+        h2d, d2h = ctypes.c_int64(0), ctypes.c_int64(0)
+        with torch.cuda.device(self.device):
+            native.ldpc_reconcile_interactive_host(self.handle, *args, B, lp, nl, int(max_iter), int(stall_window), rv,
+                                                   R, int(words), int(ctas_per_sm), int(threads), *op,
+                                                   ctypes.addressof(h2d), ctypes.addressof(d2h), self._stream())
+        return bits, iters, ok, rounds, int(h2d.value), int(d2h.value)
 
 
     def epoch_state_bytes(self, words: int, ctas_per_sm: int = 0, threads: int = 0):

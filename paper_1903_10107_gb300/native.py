@@ -45,6 +45,8 @@ SIGNATURES = {
                                        _P]),
     "ldpc_reconcile_interactive": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _I, _I, _I, _I, _P,
                                         _P, _P, _P, _P]),
+    "ldpc_reconcile_interactive_host": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _P, _I, _I, _I,
+                                             _I, _P, _P, _P, _P, _P, _P, _P]),
     "ldpc_epoch_state_bytes": (_I, [_P, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)]),
     "ldpc_reconcile_epoch": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _I, _I, _I, _P, ctypes.c_size_t,
                                   _I, _I, _I, _P, _P, _P, _P, _P]),
@@ -163,6 +165,15 @@ def ldpc_reconcile_interactive(code, bob_bits, llr_mag, rank, n_short, n_punct, 
     _call("ldpc_reconcile_interactive", code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome,
           batch, frame_list, list_len, max_iter, stall_window, reveal, max_rounds, words, ctas_per_sm, threads,
           out_bits, out_iters, out_ok, out_rounds, stream)
+
+
+def ldpc_reconcile_interactive_host(code, bob_bits, llr_mag, rank, n_short, n_punct, known, target_syndrome, batch,
+                                    frame_list, list_len, max_iter, stall_window, reveal, max_rounds, words,
+                                    ctas_per_sm, threads, out_bits, out_iters, out_ok, out_rounds, h2d_bytes,
+                                    d2h_bytes, stream):
+    _call("ldpc_reconcile_interactive_host", code, bob_bits, llr_mag, rank, n_short, n_punct, known,
+          target_syndrome, batch, frame_list, list_len, max_iter, stall_window, reveal, max_rounds, words,
+          ctas_per_sm, threads, out_bits, out_iters, out_ok, out_rounds, h2d_bytes, d2h_bytes, stream)
 
 
 def ldpc_epoch_state_bytes(code, words, ctas_per_sm, threads):

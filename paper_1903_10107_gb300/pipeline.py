@@ -10,6 +10,8 @@ sequence of batches with the copies overlapped with decoding.
 """
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import torch
 
@@ -22,10 +24,10 @@ class Reconciler:
         self.code = QCCode(base, Z, device)
         self.device = self.code.device
         self.llr_scale = float(llr_scale)
-        self.rank = None
+        self.rank = self.rank_host = None
         if tiebreak is not None:
-            rk = _rate.puncture_rank(base, Z, tiebreak)
-            self.rank = torch.from_numpy(rk).to(self.device)
+            self.rank_host = np.ascontiguousarray(_rate.puncture_rank(base, Z, tiebreak), dtype=np.int32)
+            self.rank = torch.from_numpy(self.rank_host).to(self.device)
 
     @property
     def n(self):
@@ -416,6 +418,31 @@ class InteractiveProtocol:
         revealed = rev[np.arange(B), rounds]
         return self._finish(q, p0, s0, revealed, bits, iters.astype(np.int64), ok, rounds, h2d, d2h, events)
 
+    def _run_fused_host(self, bob_h, syn_h, qber_host, known_h, timing, bits_out):
+        """All rounds in one launch from host buffers through
+        ``ldpc_reconcile_interactive_host``: the library copies the inputs in
+        and the results out."""
+        q = np.asarray(qber_host, dtype=np.float64)
+        B = q.size
+        p0, s0, rev = self.reveal_table(q)
+        out = (bits_out if bits_out is not None else torch.zeros((B, self.code.nbytes), dtype=torch.uint8),
+               torch.zeros((B,), dtype=torch.int32), torch.zeros((B,), dtype=torch.uint8),
+               torch.zeros((B,), dtype=torch.int32))
+        if timing:
+            t0 = time.perf_counter()
+        bits, iters, ok, rounds, h2d, d2h = self.code.reconcile_interactive_host(
+            bob_h, self.rec.magnitudes(q), syn_h, self.max_iter, self.rec.rank_host, s0.astype(np.int32),
+            p0.astype(np.int32), known_h, np.ascontiguousarray(rev, dtype=np.int32),
+            frame_list=np.ascontiguousarray(hardest_first(p0, s0, q), dtype=np.int32),
+            stall_window=self.stall_window, words=self.words, ctas_per_sm=self.ctas, threads=self.threads, out=out)
+        iters, ok, rounds = iters.numpy(), ok.numpy(), rounds.numpy()
+        revealed = rev[np.arange(B), rounds]
+        res = self._finish(q, p0, s0, revealed, bits.numpy(), iters.astype(np.int64), ok, rounds, 0, 0, None)
+        if timing:
+            res["call_s"] = time.perf_counter() - t0
+            res["launches"] = 1
+        return res, h2d, d2h
+
     def _run_rounds(self, bob, syn, qber_host, known, timing: bool = False, bits_out=None):
         dev = self.code.device
         n, m = self.code.n, self.code.m
@@ -479,11 +506,15 @@ class InteractiveProtocol:
         run, and the final bits, iteration counts and flags come back (the
         bits into ``bits_out`` when given, a host uint8 tensor of shape
         (frames, ceil(n/8))).  Returns (result dict as for ``run``,
-        h2d_bytes, d2h_bytes).  The copies are torch copies issued by this
-        Python layer around the C-ABI launches (the C ABI itself takes
-        device pointers)."""
+        h2d_bytes, d2h_bytes).  With all rounds in one launch (the default)
+        the library makes the copies itself, through its host-buffer entry
+        point ``ldpc_reconcile_interactive_host``; with one launch per round
+        the copies are torch copies issued by this Python layer around the
+        C-ABI launches."""
         if isinstance(bits_out, str):
             raise ValueError("run_host returns the bits to the host: bits_out must be None or a host tensor")
+        if self.fused:
+            return self._run_fused_host(bob_h, syn_h, qber_host, known_h, timing, bits_out)
         dev = self.code.device
         d = [t.to(dev, non_blocking=True) for t in (bob_h, syn_h, known_h)]
         h2d = sum(int(t.numel() * t.element_size()) for t in (bob_h, syn_h, known_h))

@@ -37,6 +37,13 @@ def test_library_exports_every_declared_symbol():
     assert set(native.SIGNATURES) >= _declared()
 
 
+def test_binding_wraps_every_entry_point():
+    """native.py has a function of the same name for every entry point (the
+    error-string getters are read through the loaded library)."""
+    missing = [k for k in native.SIGNATURES if not callable(getattr(native, k, None))]
+    assert sorted(missing) == ["ldpc_last_error", "ldpc_strerror"]
+
+
 def test_error_paths_without_gpu():
     lib = native.load()
     assert lib.ldpc_strerror(native.LDPC_EINVAL) == b"invalid argument"
@@ -48,6 +55,10 @@ def test_error_paths_without_gpu():
     assert lib.ldpc_code_info(None, None, None, None, None) == native.LDPC_EINVAL
     assert lib.ldpc_decode_batch(None, None, None, 1, 5, None, None, None, None) == native.LDPC_EINVAL
     assert lib.ldpc_debug_tau_table(None, None) == native.LDPC_EINVAL
+    # the host-buffer interactive entry checks its arguments before any copy
+    args = [None] * 8 + [1, None, 1, 5, 0, None, 0, 1, 1, 0] + [None] * 7
+    assert lib.ldpc_reconcile_interactive_host(*args) == native.LDPC_EINVAL
+    assert b"NULL code" in lib.ldpc_last_error()
 
 
 def test_product_rate_plan_matches_closed_form():

@@ -138,3 +138,45 @@ def test_host_stream_overlapped_batches_match_oracle():
         ob, oi, oo, _ = orc.decode(base, Z, llr, orc.syndrome(base, Z, xa_u), 50)
         assert np.array_equal(ok.numpy(), oo) and np.array_equal(iters.numpy(), oi)
         assert np.array_equal(inputs.unpack_bits(bits.numpy(), n), ob)
+
+
+def test_host_buffer_entry_point_matches_device_entry():
+    """ldpc_reconcile_interactive_host (host buffers in and out, the library's
+    own copies) against ldpc_reconcile_interactive on device copies of the
+    same inputs: equal bits, iterations, flags and rounds; pageable numpy
+    inputs work; the byte counts are exactly the arrays copied; frames the
+    list leaves out keep the caller's output values."""
+    from paper_1903_10107_gb300.pipeline import InteractiveProtocol, Reconciler, hardest_first
+    B = 40
+    base, Z, n, m, q, xa, yb, tb = _code_and_frames(B, seed=13)
+    rec = Reconciler(base, Z, tb, llr_scale=SCALE)
+    code = rec.code
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    syn = code.syndrome(c(xa))
+    proto = InteractiveProtocol(rec, 40, f_start=1.1, df=0.15, max_rounds=4, stall_window=6)
+    p0, s0, rev = proto.reveal_table(q)
+    mag = rec.magnitudes(q)
+    order = hardest_first(p0, s0, q).astype(np.int32)
+    rev32 = np.ascontiguousarray(rev, dtype=np.int32)
+    dev = code.reconcile_interactive(c(yb), c(mag), syn, 40, rec.rank, c(s0.astype(np.int32)),
+                                     c(p0.astype(np.int32)), c(xa), c(rev32), frame_list=c(order), stall_window=6)
+    dev = [t.cpu().numpy() for t in dev]
+    syn_h = syn.cpu().numpy()
+    host = code.reconcile_interactive_host(yb, mag, syn_h, 40, rec.rank_host, s0.astype(np.int32),
+                                           p0.astype(np.int32), xa, rev32, frame_list=order, stall_window=6)
+    for a, b in zip(dev, host[:4]):
+        assert np.array_equal(a, b.numpy())
+    nb, mb = code.nbytes, code.mbytes
+    assert host[4] == 2 * B * nb + B * mb + B + 8 * B + 4 * rev32.size + 4 * n + 4 * B
+    assert host[5] == B * nb + 9 * B
+    # a list of the first half only: the other frames' outputs are the caller's
+    half = order[: B // 2]
+    out = (torch.full((B, nb), 0xA5, dtype=torch.uint8).pin_memory(), torch.full((B,), -7, dtype=torch.int32),
+           torch.full((B,), 3, dtype=torch.uint8), torch.full((B,), -9, dtype=torch.int32))
+    part = code.reconcile_interactive_host(yb, mag, syn_h, 40, rec.rank_host, s0.astype(np.int32),
+                                           p0.astype(np.int32), xa, rev32, frame_list=half, stall_window=6, out=out)
+    rest = np.setdiff1d(np.arange(B), half)
+    assert (part[0].numpy()[rest] == 0xA5).all() and (part[1].numpy()[rest] == -7).all()
+    assert (part[2].numpy()[rest] == 3).all() and (part[3].numpy()[rest] == -9).all()
+    for a, b in zip(dev, part[:4]):
+        assert np.array_equal(a[half], b.numpy()[half])
