@@ -155,3 +155,12 @@ def test_interactive_protocol_full_size_sampled_frames_match_oracle():
     assert np.array_equal(inputs.unpack_bits(bits[sel], w.n), ref["bits"])
     for k in ("ok", "iters", "rounds", "revealed", "key_bits"):
         assert np.array_equal(np.asarray(res[k])[sel], np.asarray(ref[k])), k
+    # the benchmark's end-to-end path: the same step from pinned host buffers through the C-ABI
+    # host-buffer call gives every frame the same result
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_bits = torch.empty((B, rec.code.nbytes), dtype=torch.uint8, pin_memory=True)
+    hres, h2d, d2h = proto.run_host(pin(yb), syn.cpu().pin_memory(), q, pin(xa), bits_out=h_bits)
+    assert np.array_equal(hres["bits"], bits)
+    for k in ("ok", "iters", "rounds", "revealed", "key_bits"):
+        assert np.array_equal(np.asarray(hres[k]), np.asarray(res[k])), k
+    assert d2h == B * rec.code.nbytes + 9 * B and h2d > 2 * B * rec.code.nbytes
