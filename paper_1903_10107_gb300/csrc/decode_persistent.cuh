@@ -349,7 +349,13 @@ __global__ void __launch_bounds__(MAXT) persistent_kernel(PersistArgs A) {
             int i = q / Z, r = q - i * Z;
             const int di = QT / Z, dr = QT - di * Z;
             for (int c = q; c < m; c += QT) {
-                const uint32_t p = ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
+                uint32_t p;
+                if constexpr (MAXH <= 8) {  // rows of at most 16 edges
+                    p = ldpc_dev::row_parity_unrolled<W, 2 * MAXH>(E_s, TB.et + off[i], deg[i], r, Z, w,
+                                                                   syn_s[c * W + w]);
+                } else {
+                    p = ldpc_dev::row_parity<W>(E_s, TB.et + off[i], deg[i], r, Z, w, syn_s[c * W + w]);
+                }
                 bad |= p;
                 if (A.stall) {
                     ulo += (p >> 7) & 0x00010001u;

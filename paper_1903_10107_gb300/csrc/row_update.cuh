@@ -183,4 +183,25 @@ __device__ __forceinline__ uint32_t row_parity(const uint32_t* E_s, const int2* 
     return p & kHigh;
 }
 
+// row_parity with the edge loop unrolled for at most MAXD edges: every soft-value load of the row is in
+// flight before the first is used.  Worth it where the unrolled loads fit the registers without spilling
+// (codes whose rows have at most 16 edges): 0.7-0.8 % on the persistent step of the n = 49152 code.
+template <int W, int MAXD>
+__device__ __forceinline__ uint32_t row_parity_unrolled(const uint32_t* E_s, const int2* et, int d, int r, int Z,
+                                                        int w, uint32_t syn_nib) {
+    uint32_t v[MAXD];
+#pragma unroll
+    for (int k = 0; k < MAXD; ++k) {
+        if (k < d) {
+            const int2 t = et[k];
+            v[k] = E_s[t.x + wrap(r + t.y, Z) * W + w];
+        }
+    }
+    uint32_t p = nibble_to_high(syn_nib) ^ ((d & 1) ? kHigh : 0u);
+#pragma unroll
+    for (int k = 0; k < MAXD; ++k)
+        if (k < d) p ^= v[k];
+    return p & kHigh;
+}
+
 }  // namespace ldpc_dev
