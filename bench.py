@@ -73,7 +73,11 @@ def parse_args(argv=None):
                     help="fixed protocol: the mixed-rate workload's target efficiency (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-secondary", action="store_true", help="skip the fixed-rate line beside the default")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the fixed-rate line and the second starting efficiency beside the default")
+    ap.add_argument("--alt-f-start", type=float, default=1.25,
+                    help="a second starting efficiency for the interactive protocol, reported beside the default "
+                         "(0 = none)")
     ap.add_argument("--no-order", action="store_true", help="persistent launch takes frames in index order")
     ap.add_argument("--separate-rounds", action="store_true",
                     help="interactive: one launch per round (host reads the flags between rounds)")
@@ -613,6 +617,35 @@ def run_ours(args, rank, world, dist):
             e2e_s = (time.perf_counter() - t0) / e2e_steps
             ecorr = eres["ok"].astype(bool) & np.all(inputs.unpack_bits(eres["bits"], w.n) == xa_bits, axis=1)
             e2e = (e2e_s, float(eres["key_bits"][ecorr].sum()), h2d, d2h)
+        if not args.no_secondary and args.alt_f_start > 0:
+            # the same protocol from a second starting efficiency, device-timed like the default
+            alt = InteractiveProtocol(rec, w.max_iter, f_start=args.alt_f_start, df=args.df,
+                                      max_rounds=args.max_rounds, stall_window=args.stall_window, words=words,
+                                      ctas_per_sm=ctas, threads=threads)
+            for _ in range(2):
+                alt.run(dv["yb"], dv["syn"], bt.q, d_known, bits_out="device")
+            torch.cuda.synchronize()
+            a_steps, a_kern = [], []
+            for _ in range(max(3, min(args.steps, 5))):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ares = alt.run(dv["yb"], dv["syn"], bt.q, d_known, timing=True, bits_out="device")
+                e1.record(stream)
+                torch.cuda.synchronize()
+                a_steps.append(e0.elapsed_time(e1) / 1e3)
+                a_kern.append(ares["kernel_s"])
+            acorr = ares["ok"].astype(bool) & np.all(inputs.unpack_bits(ares["bits"].cpu().numpy(), w.n) == xa_bits,
+                                                     axis=1)
+            a_s, a_it = float(np.mean(a_steps)), float(ares["iters"].sum())
+            a_alg = a_it * 2.0 * code.edges + persistent_io_bytes(code, float((ares["rounds"] + 1).sum()))
+            extra_keys["alt_start"] = {
+                "f_start": args.alt_f_start, "value": float(ares["key_bits"][acorr].sum()) / a_s / 1e6, "unit": "Mbps",
+                "ms_per_step": a_s * 1e3, "fer": 1.0 - float(acorr.mean()),
+                "efficiency_f_mean": float(ares["f"][acorr].mean()) if acorr.any() else None,
+                "rounds_mean": float(ares["rounds"].mean()), "iters_mean_total": float(ares["iters"].mean()),
+                "roofline": roofline_hbm(a_alg, float(np.mean(a_kern)), "persistent_kernel", None),
+                "note": "the default protocol started from f_start instead of 1.1: the same final efficiency "
+                        "range is reached with fewer hopeless rounds"}
     else:
         barrier()
         clocks.start()
