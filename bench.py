@@ -603,16 +603,20 @@ def run_ours(args, rank, world, dist):
                   "work_order": "hardest first (most punctured, highest QBER)"}
         # end to end from pinned host buffers through InteractiveProtocol.run_host
         e2e = None
+        e2e_each = []
         if not args.no_e2e:
             pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
             h_yb, h_syn, h_kn = pin(bt.yb), dv["syn"].cpu().pin_memory(), pin(bt.xa)
             h_bits = torch.empty((B, code.nbytes), dtype=torch.uint8, pin_memory=True)
             proto.run_host(h_yb, h_syn, bt.q, h_kn, bits_out=h_bits)
             torch.cuda.synchronize()
-            e2e_steps = max(2, min(args.steps, 3))
+            e2e_steps = max(2, min(args.steps, 5))
+            e2e_each = []
             t0 = time.perf_counter()
             for _ in range(e2e_steps):
+                ts = time.perf_counter()
                 eres, h2d, d2h = proto.run_host(h_yb, h_syn, bt.q, h_kn, bits_out=h_bits)
+                e2e_each.append(time.perf_counter() - ts)
             torch.cuda.synchronize()
             e2e_s = (time.perf_counter() - t0) / e2e_steps
             ecorr = eres["ok"].astype(bool) & np.all(inputs.unpack_bits(eres["bits"], w.n) == xa_bits, axis=1)
@@ -661,6 +665,7 @@ def run_ours(args, rank, world, dist):
                       "iters_mean": float(fr["iters"].mean()), "processed_key_mbps": all_key / step_s / 1e6}
         launch = fr["launch"]
         e2e = None
+        e2e_each = []
         if not args.no_e2e:
             e2e = measure_fixed_e2e(args, rec, bt, dv["syn"], dev, launch)
 
@@ -686,6 +691,7 @@ def run_ours(args, rank, world, dist):
                                      torch.cuda.get_device_properties(dev).multi_processor_count),
         "e2e": {"value": e_tot / e2e_max / 1e6 if e2e is not None else None, "unit": "Mbps",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "step_ms": [round(1e3 * x, 2) for x in e2e_each] if e2e_each else None,
                 "path": ("the C-ABI host-buffer call ldpc_reconcile_interactive_host (via InteractiveProtocol."
                          "run_host): pinned host buffers in and out, the library's own copies around its one "
                          "launch" if inter and not args.separate_rounds else
