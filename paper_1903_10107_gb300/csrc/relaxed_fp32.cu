@@ -110,42 +110,60 @@ __device__ __forceinline__ void row_forward(float* E, const float* Lold, float* 
                                             int d, int half, int r, int Z, float S, float al, float ga, float kap,
                                             float ikap) {
     const RowHalf H = row_half(d, half);
+    // Slots guarded in chunks (as in the integer row update): a chunk wholly
+    // past the walk's count is one branch (backward 7 %, forward 2 % faster on
+    // the n = 4096 code, rows of up to 18 edges).
+    constexpr int CH = HMAX <= 8 ? HMAX : 4;
     float v[HMAX], O[HMAX];
     int idx[HMAX];
     float sgn = 1.0f;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < H.cnt) {
-            const int k = H.k0 + j * H.kdir;
-            const int2 t = et[k];
-            idx[j] = t.x + ldpc_dev::wrap(r + t.y, Z);
-            v[j] = E[idx[j]] - (Lold ? Lold[(size_t)k * Z] : 0.0f);  // Eq. 8
-            if (v[j] < 0.0f) sgn = -sgn;                              // Eq. 1
-            if (Vout) Vout[(size_t)k * Z] = v[j];
+#pragma unroll
+    for (int c0 = 0; c0 < HMAX; c0 += CH) {
+        if (c0 < H.cnt) {
+#pragma unroll
+            for (int j = c0; j < (c0 + CH < HMAX ? c0 + CH : HMAX); ++j) {
+                if (j < H.cnt) {
+                    const int k = H.k0 + j * H.kdir;
+                    const int2 t = et[k];
+                    idx[j] = t.x + ldpc_dev::wrap(r + t.y, Z);
+                    v[j] = E[idx[j]] - (Lold ? Lold[(size_t)k * Z] : 0.0f);  // Eq. 8
+                    if (v[j] < 0.0f) sgn = -sgn;                              // Eq. 1
+                    if (Vout) Vout[(size_t)k * Z] = v[j];
+                }
+            }
         }
     }
     float tot = kEmpty;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < H.cnt) {
-            const float a = fabsf(v[j]);
-            tot = (j == 0) ? a : bplus(tot, a, kap, ikap);
-            O[j] = tot;
+#pragma unroll
+    for (int c0 = 0; c0 < HMAX; c0 += CH) {
+        if (c0 < H.cnt) {
+#pragma unroll
+            for (int j = c0; j < (c0 + CH < HMAX ? c0 + CH : HMAX); ++j) {
+                if (j < H.cnt) {
+                    const float a = fabsf(v[j]);
+                    tot = (j == 0) ? a : bplus(tot, a, kap, ikap);
+                    O[j] = tot;
+                }
+            }
         }
     }
     float X = __shfl_xor_sync(0xffffffffu, tot, 1);
     S *= sgn * __shfl_xor_sync(0xffffffffu, sgn, 1);
-#pragma unroll(HMAX)
-    for (int jj = 0; jj < HMAX; ++jj) {
-        const int j = HMAX - 1 - jj;
-        if (j < H.cnt) {
-            const int k = H.k0 + j * H.kdir;
-            const float B = (j == 0) ? X : bplus(O[j >= 1 ? j - 1 : 0], X, kap, ikap);
-            if (j > 0) X = bplus(fabsf(v[j]), X, kap, ikap);
-            const float mag = al * fmaxf(B - ga, 0.0f);
-            const float Ln = (v[j] < 0.0f ? -S : S) * mag;  // own sign removed
-            E[idx[j]] = v[j] + Ln;                          // Eq. 9
-            if (Lnew) Lnew[(size_t)k * Z] = Ln;
+#pragma unroll
+    for (int c0 = ((HMAX - 1) / CH) * CH; c0 >= 0; c0 -= CH) {
+        if (c0 < H.cnt) {
+#pragma unroll
+            for (int j = (c0 + CH < HMAX ? c0 + CH : HMAX) - 1; j >= c0; --j) {
+                if (j < H.cnt) {
+                    const int k = H.k0 + j * H.kdir;
+                    const float B = (j == 0) ? X : bplus(O[j >= 1 ? j - 1 : 0], X, kap, ikap);
+                    if (j > 0) X = bplus(fabsf(v[j]), X, kap, ikap);
+                    const float mag = al * fmaxf(B - ga, 0.0f);
+                    const float Ln = (v[j] < 0.0f ? -S : S) * mag;  // own sign removed
+                    E[idx[j]] = v[j] + Ln;                          // Eq. 9
+                    if (Lnew) Lnew[(size_t)k * Z] = Ln;
+                }
+            }
         }
     }
 }
@@ -158,37 +176,52 @@ __device__ __forceinline__ void row_backward(float* G, const float* Vrow, float*
                                              int dtrue, int half, int r, int Z, float S, float al, float ga,
                                              float kap, float ikap, float& acc_a, float& acc_g) {
     const RowHalf H = row_half(d, half);
+    constexpr int CH = HMAX <= 8 ? HMAX : 4;  // slots per guarded chunk
     float a[HMAX], O[HMAX], X[HMAX], gO[HMAX], gA[HMAX];
     uint32_t neg = 0;  // bit j: v_j < 0
     float sgn = 1.0f;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < H.cnt) {
-            const float v = Vrow[(size_t)(H.k0 + j * H.kdir) * Z];
-            a[j] = fabsf(v);
-            if (v < 0.0f) {
-                neg |= 1u << j;
-                sgn = -sgn;
+#pragma unroll
+    for (int c0 = 0; c0 < HMAX; c0 += CH) {
+        if (c0 < H.cnt) {
+#pragma unroll
+            for (int j = c0; j < (c0 + CH < HMAX ? c0 + CH : HMAX); ++j) {
+                if (j < H.cnt) {
+                    const float v = Vrow[(size_t)(H.k0 + j * H.kdir) * Z];
+                    a[j] = fabsf(v);
+                    if (v < 0.0f) {
+                        neg |= 1u << j;
+                        sgn = -sgn;
+                    }
+                    gO[j] = gA[j] = 0.0f;
+                }
             }
-            gO[j] = gA[j] = 0.0f;
         }
     }
     float tot = kEmpty;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < H.cnt) {
-            tot = (j == 0) ? a[j] : bplus(tot, a[j], kap, ikap);
-            O[j] = tot;
+#pragma unroll
+    for (int c0 = 0; c0 < HMAX; c0 += CH) {
+        if (c0 < H.cnt) {
+#pragma unroll
+            for (int j = c0; j < (c0 + CH < HMAX ? c0 + CH : HMAX); ++j) {
+                if (j < H.cnt) {
+                    tot = (j == 0) ? a[j] : bplus(tot, a[j], kap, ikap);
+                    O[j] = tot;
+                }
+            }
         }
     }
     float x = __shfl_xor_sync(0xffffffffu, tot, 1);
     S *= sgn * __shfl_xor_sync(0xffffffffu, sgn, 1);
-#pragma unroll(HMAX)
-    for (int jj = 0; jj < HMAX; ++jj) {  // partner chain beyond every slot
-        const int j = HMAX - 1 - jj;
-        if (j < H.cnt) {
-            X[j] = x;
-            if (j > 0) x = bplus(a[j], x, kap, ikap);
+#pragma unroll
+    for (int c0 = ((HMAX - 1) / CH) * CH; c0 >= 0; c0 -= CH) {  // partner chain beyond every slot
+        if (c0 < H.cnt) {
+#pragma unroll
+            for (int j = (c0 + CH < HMAX ? c0 + CH : HMAX) - 1; j >= c0; --j) {
+                if (j < H.cnt) {
+                    X[j] = x;
+                    if (j > 0) x = bplus(a[j], x, kap, ikap);
+                }
+            }
         }
     }
     // Ascending: the magnitude m_j = beta(O_{j-1}, X_j) of every slot and its
@@ -196,28 +229,33 @@ __device__ __forceinline__ void row_backward(float* G, const float* Vrow, float*
     // beta(a_j, X_j), carried as one running value g (the adjoint of X_j);
     // what reaches the far end belongs to the partner's fold total.
     float g = 0.0f;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < H.cnt) {
-            const int k = H.k0 + j * H.kdir;
-            const int2 t = et[k];
-            const float B = (j == 0) ? X[0] : bplus(O[j >= 1 ? j - 1 : 0], X[j], kap, ikap);
-            const float sj = ((neg >> j) & 1u) ? -S : S;
-            const float gtot = gLrow[(size_t)k * Z] + G[t.x + ldpc_dev::wrap(r + t.y, Z)];  // L_new feeds E and the next iteration
-            const float gmag = gtot * sj;
-            const bool pos = B > ga;
-            acc_a += gmag * fmaxf(B - ga, 0.0f);
-            acc_g -= pos ? gmag * al : 0.0f;
-            const float gm = (pos && dtrue > 1) ? gmag * al : 0.0f;
-            if (j == 0) {
-                g = gm;
-            } else {
-                float dx, dy, cx, cy;
-                bplus_grad(O[j >= 1 ? j - 1 : 0], X[j], ikap, dx, dy);
-                gO[j >= 1 ? j - 1 : 0] += gm * dx;
-                bplus_grad(a[j], X[j], ikap, cx, cy);
-                gA[j] += g * cx;
-                g = gm * dy + g * cy;
+#pragma unroll
+    for (int c0 = 0; c0 < HMAX; c0 += CH) {
+        if (c0 < H.cnt) {
+#pragma unroll
+            for (int j = c0; j < (c0 + CH < HMAX ? c0 + CH : HMAX); ++j) {
+                if (j < H.cnt) {
+                    const int k = H.k0 + j * H.kdir;
+                    const int2 t = et[k];
+                    const float B = (j == 0) ? X[0] : bplus(O[j >= 1 ? j - 1 : 0], X[j], kap, ikap);
+                    const float sj = ((neg >> j) & 1u) ? -S : S;
+                    const float gtot = gLrow[(size_t)k * Z] + G[t.x + ldpc_dev::wrap(r + t.y, Z)];  // L_new feeds E and the next iteration
+                    const float gmag = gtot * sj;
+                    const bool pos = B > ga;
+                    acc_a += gmag * fmaxf(B - ga, 0.0f);
+                    acc_g -= pos ? gmag * al : 0.0f;
+                    const float gm = (pos && dtrue > 1) ? gmag * al : 0.0f;
+                    if (j == 0) {
+                        g = gm;
+                    } else {
+                        float dx, dy, cx, cy;
+                        bplus_grad(O[j >= 1 ? j - 1 : 0], X[j], ikap, dx, dy);
+                        gO[j >= 1 ? j - 1 : 0] += gm * dx;
+                        bplus_grad(a[j], X[j], ikap, cx, cy);
+                        gA[j] += g * cx;
+                        g = gm * dy + g * cy;
+                    }
+                }
             }
         }
     }
@@ -225,26 +263,30 @@ __device__ __forceinline__ void row_backward(float* G, const float* Vrow, float*
     // adjoint of the total that the partner's chain sends back; each slot's
     // adjoint is complete once its step is done, so it is written out there.
     float go = __shfl_xor_sync(0xffffffffu, g, 1);
-#pragma unroll(HMAX)
-    for (int jj = 0; jj < HMAX; ++jj) {
-        const int j = HMAX - 1 - jj;
-        if (j < H.cnt) {
-            go += gO[j];
-            float ga_j = gA[j];
-            if (j > 0) {
-                float dx, dy;
-                bplus_grad(O[j >= 1 ? j - 1 : 0], a[j], ikap, dx, dy);
-                ga_j += go * dy;
-                go *= dx;
-            } else {
-                ga_j += go;
+#pragma unroll
+    for (int c0 = ((HMAX - 1) / CH) * CH; c0 >= 0; c0 -= CH) {
+        if (c0 < H.cnt) {
+#pragma unroll
+            for (int j = (c0 + CH < HMAX ? c0 + CH : HMAX) - 1; j >= c0; --j) {
+                if (j < H.cnt) {
+                    go += gO[j];
+                    float ga_j = gA[j];
+                    if (j > 0) {
+                        float dx, dy;
+                        bplus_grad(O[j >= 1 ? j - 1 : 0], a[j], ikap, dx, dy);
+                        ga_j += go * dy;
+                        go *= dx;
+                    } else {
+                        ga_j += go;
+                    }
+                    const int k = H.k0 + j * H.kdir;
+                    const int2 t = et[k];
+                    const int vi = t.x + ldpc_dev::wrap(r + t.y, Z);
+                    const float gv = G[vi] + ga_j * (((neg >> j) & 1u) ? -1.0f : 1.0f);  // d|v|/dv = sign(v)
+                    G[vi] = gv;                                                         // adjoint of E before the layer
+                    gLrow[(size_t)k * Z] = -gv;                                         // adjoint of the old message (Eq. 8)
+                }
             }
-            const int k = H.k0 + j * H.kdir;
-            const int2 t = et[k];
-            const int vi = t.x + ldpc_dev::wrap(r + t.y, Z);
-            const float gv = G[vi] + ga_j * (((neg >> j) & 1u) ? -1.0f : 1.0f);  // d|v|/dv = sign(v)
-            G[vi] = gv;                                                         // adjoint of E before the layer
-            gLrow[(size_t)k * Z] = -gv;                                         // adjoint of the old message (Eq. 8)
         }
     }
 }
