@@ -241,6 +241,7 @@ __device__ __forceinline__ void row_update_words(uint32_t* E_s, uint32_t* msg, c
     d = valid ? d : 0;
     const int h = (d + 1) >> 1;
     const int cnt = half ? d - h : h;
+    constexpr int CH = HMAX <= 8 ? HMAX : 4;  // slots per guarded chunk, as in row_update (2-4 % here)
     const int k0 = half ? d - 1 : 0;
     const int kdir = half ? -1 : 1;
     const int2* et = etab + k0;
@@ -252,36 +253,46 @@ __device__ __forceinline__ void row_update_words(uint32_t* E_s, uint32_t* msg, c
 #pragma unroll
     for (int w = 0; w < W; ++w) S[w] = (half == 0 && valid) ? nibble_to_high(syn_row[w]) : 0u;
     const bool load_l = fresh != 0xFFFFFFFFu;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < cnt) {
-            if (load_l) {
-                ld_words<W>(Lp + j * Lstep, av[j]);  // every message load of the row in flight first
-            } else {
 #pragma unroll
-                for (int w = 0; w < W; ++w) av[j][w] = kHigh;
+    for (int c0 = 0; c0 < HMAX; c0 += CH) {
+        if (c0 < cnt) {
+#pragma unroll
+            for (int j = c0; j < (c0 + CH < HMAX ? c0 + CH : HMAX); ++j) {
+                if (j < cnt) {
+                    if (load_l) {
+                        ld_words<W>(Lp + j * Lstep, av[j]);  // every message load of the row in flight first
+                    } else {
+        #pragma unroll
+                        for (int w = 0; w < W; ++w) av[j][w] = kHigh;
+                    }
+                    const int2 t = et[j * kdir];
+                    idx[j] = t.x + ldpc_dev::wrap(r + t.y, Z) * W;
+                }
             }
-            const int2 t = et[j * kdir];
-            idx[j] = t.x + ldpc_dev::wrap(r + t.y, Z) * W;
         }
     }
     uint32_t tot[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) tot[w] = kMax;
-#pragma unroll(HMAX)
-    for (int j = 0; j < HMAX; ++j) {
-        if (j < cnt) {
-            uint32_t e[W];
-            ld_words<W>(&E_s[idx[j]], e);
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const uint32_t lb = select(fresh, kHigh, av[j][w]);  // stale lanes read as 0
-                const uint32_t sv = lt_u8(e[w], lb);
-                const uint32_t a = cap127(absdiff(e[w], lb));
-                av[j][w] = a | sv;
-                S[w] ^= sv;
-                tot[w] = (j == 0) ? a : tau(tot[w], a);
-                F[j][w] = tot[w];
+    for (int c0 = 0; c0 < HMAX; c0 += CH) {
+        if (c0 < cnt) {
+#pragma unroll
+            for (int j = c0; j < (c0 + CH < HMAX ? c0 + CH : HMAX); ++j) {
+                if (j < cnt) {
+                    uint32_t e[W];
+                    ld_words<W>(&E_s[idx[j]], e);
+        #pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        const uint32_t lb = select(fresh, kHigh, av[j][w]);  // stale lanes read as 0
+                        const uint32_t sv = lt_u8(e[w], lb);
+                        const uint32_t a = cap127(absdiff(e[w], lb));
+                        av[j][w] = a | sv;
+                        S[w] ^= sv;
+                        tot[w] = (j == 0) ? a : tau(tot[w], a);
+                        F[j][w] = tot[w];
+                    }
+                }
             }
         }
     }
@@ -292,28 +303,32 @@ __device__ __forceinline__ void row_update_words(uint32_t* E_s, uint32_t* msg, c
         S[w] ^= __shfl_xor_sync(0xffffffffu, S[w], 1);
         MS[w] = spread(S[w]);
     }
-#pragma unroll(HMAX)
-    for (int jj = 0; jj < HMAX; ++jj) {
-        const int j = HMAX - 1 - jj;
-        if (j < cnt) {
-            uint32_t eo[W], en[W], ln[W];
-            ld_words<W>(&E_s[idx[j]], eo);
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const uint32_t a = av[j][w] & kMax;
-                const uint32_t Fp = F[j >= 1 ? j - 1 : 0][w];
-                uint32_t m = (j == 0) ? R[w] : tau(Fp, R[w]);
-                if (j > 0) R[w] = tau(a, R[w]);
-                if (TABLES) m = ldpc_dev::apply_table(m, sq, oq);
-                const uint32_t Msv = spread(av[j][w]);
-                const uint32_t hm = kHigh | m;
-                ln[w] = select(Msv ^ MS[w], 0x01010100u - hm, hm);
-                const uint32_t y = select(MS[w], kHigh + a - m, kHigh | cap127(a + m));
-                const uint32_t sat = spread(absdiff(eo[w], kHigh) + kOnes);  // |E| = 127
-                en[w] = select(act[w] & ~sat, select(Msv, 0x01010100u - y, y), eo[w]);
+    for (int c0 = ((HMAX - 1) / CH) * CH; c0 >= 0; c0 -= CH) {
+        if (c0 < cnt) {
+#pragma unroll
+            for (int j = (c0 + CH < HMAX ? c0 + CH : HMAX) - 1; j >= c0; --j) {
+                if (j < cnt) {
+                    uint32_t eo[W], en[W], ln[W];
+                    ld_words<W>(&E_s[idx[j]], eo);
+        #pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        const uint32_t a = av[j][w] & kMax;
+                        const uint32_t Fp = F[j >= 1 ? j - 1 : 0][w];
+                        uint32_t m = (j == 0) ? R[w] : tau(Fp, R[w]);
+                        if (j > 0) R[w] = tau(a, R[w]);
+                        if (TABLES) m = ldpc_dev::apply_table(m, sq, oq);
+                        const uint32_t Msv = spread(av[j][w]);
+                        const uint32_t hm = kHigh | m;
+                        ln[w] = select(Msv ^ MS[w], 0x01010100u - hm, hm);
+                        const uint32_t y = select(MS[w], kHigh + a - m, kHigh | cap127(a + m));
+                        const uint32_t sat = spread(absdiff(eo[w], kHigh) + kOnes);  // |E| = 127
+                        en[w] = select(act[w] & ~sat, select(Msv, 0x01010100u - y, y), eo[w]);
+                    }
+                    st_words<W>(&E_s[idx[j]], en);
+                    st_words<W>(Lp + j * Lstep, ln);
+                }
             }
-            st_words<W>(&E_s[idx[j]], en);
-            st_words<W>(Lp + j * Lstep, ln);
         }
     }
 }
