@@ -391,15 +391,31 @@ class InteractiveProtocol:
             torch.cuda.current_stream(bits.device).synchronize()
         return bits_out.numpy(), int(bits.numel())
 
+    def _stage(self, key, a):
+        """Numpy array ``a`` copied into a page-locked host tensor kept per
+        key (reused while the shape and type stay), so that the control
+        arrays of a step move by DMA.  Every caller synchronises before the
+        next step, so a buffer is never overwritten while a copy reads it."""
+        a = np.ascontiguousarray(a)
+        cache = self.__dict__.setdefault("_pinned", {})
+        t = cache.get(key)
+        if t is None or tuple(t.shape) != a.shape or t.numpy().dtype != a.dtype:
+            t = torch.from_numpy(np.empty_like(a))
+            if torch.cuda.is_available():
+                t = t.pin_memory()
+            cache[key] = t
+        t.numpy()[...] = a
+        return t
+
     def _run_fused(self, bob, syn, qber_host, known, timing, bits_out=None):
         dev = self.code.device
         q = np.asarray(qber_host, dtype=np.float64)
         B = q.size
         p0, s0, rev = self.reveal_table(q)
-        c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-        d_mag, d_p0, d_s0 = c(self.rec.magnitudes(q)), c(p0.astype(np.int32)), c(s0.astype(np.int32))
-        d_rev = c(rev.astype(np.int32))
-        d_list = c(hardest_first(p0, s0, q))
+        c = lambda k, a: self._stage(k, a).to(dev, non_blocking=True)
+        d_mag, d_p0 = c("mag", self.rec.magnitudes(q)), c("p0", p0.astype(np.int32))
+        d_s0, d_rev = c("s0", s0.astype(np.int32)), c("rev", rev.astype(np.int32))
+        d_list = c("list", hardest_first(p0, s0, q).astype(np.int32))
         h2d = B + 8 * B + 4 * rev.size + 4 * B
         events = None
         if timing:
@@ -431,9 +447,10 @@ class InteractiveProtocol:
         if timing:
             t0 = time.perf_counter()
         bits, iters, ok, rounds, h2d, d2h = self.code.reconcile_interactive_host(
-            bob_h, self.rec.magnitudes(q), syn_h, self.max_iter, self.rec.rank_host, s0.astype(np.int32),
-            p0.astype(np.int32), known_h, np.ascontiguousarray(rev, dtype=np.int32),
-            frame_list=np.ascontiguousarray(hardest_first(p0, s0, q), dtype=np.int32),
+            bob_h, self._stage("mag", self.rec.magnitudes(q)), syn_h, self.max_iter,
+            self._stage("rank", self.rec.rank_host), self._stage("s0", s0.astype(np.int32)),
+            self._stage("p0", p0.astype(np.int32)), known_h, self._stage("rev", rev.astype(np.int32)),
+            frame_list=self._stage("list", hardest_first(p0, s0, q).astype(np.int32)),
             stall_window=self.stall_window, words=self.words, ctas_per_sm=self.ctas, threads=self.threads, out=out)
         iters, ok, rounds = iters.numpy(), ok.numpy(), rounds.numpy()
         revealed = rev[np.arange(B), rounds]
