@@ -187,6 +187,8 @@ __device__ __forceinline__ void row_backward(float* G, const float* Vrow, float*
             for (int j = c0; j < (c0 + CH < HMAX ? c0 + CH : HMAX); ++j) {
                 if (j < H.cnt) {
                     const float v = Vrow[(size_t)(H.k0 + j * H.kdir) * Z];
+                    // the message adjoint this slot reads in the ascending pass, fetched into L1 now
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(gLrow + (size_t)(H.k0 + j * H.kdir) * Z));
                     a[j] = fabsf(v);
                     if (v < 0.0f) {
                         neg |= 1u << j;
