@@ -126,9 +126,9 @@ __device__ __forceinline__ void row_forward(float* E, const float* Lold, float* 
                     const int k = H.k0 + j * H.kdir;
                     const int2 t = et[k];
                     idx[j] = t.x + ldpc_dev::wrap(r + t.y, Z);
-                    v[j] = E[idx[j]] - (Lold ? Lold[(size_t)k * Z] : 0.0f);  // Eq. 8
+                    v[j] = E[idx[j]] - (Lold ? Lold[k * Z] : 0.0f);  // Eq. 8
                     if (v[j] < 0.0f) sgn = -sgn;                              // Eq. 1
-                    if (Vout) Vout[(size_t)k * Z] = v[j];
+                    if (Vout) Vout[k * Z] = v[j];
                 }
             }
         }
@@ -161,7 +161,7 @@ __device__ __forceinline__ void row_forward(float* E, const float* Lold, float* 
                     const float mag = al * fmaxf(B - ga, 0.0f);
                     const float Ln = (v[j] < 0.0f ? -S : S) * mag;  // own sign removed
                     E[idx[j]] = v[j] + Ln;                          // Eq. 9
-                    if (Lnew) Lnew[(size_t)k * Z] = Ln;
+                    if (Lnew) Lnew[k * Z] = Ln;
                 }
             }
         }

@@ -91,7 +91,7 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
     const int kdir = half ? -1 : 1;
     const int2* et = C.et + k0;
     uint32_t* Lp = C.msg + ((size_t)(C.b0 + k0) * Z + r) * W + C.w;
-    const ptrdiff_t Lstep = (ptrdiff_t)kdir * Z * W;
+    const int Lstep = kdir * Z * W;  // 32-bit: one wide multiply-add per slot address
     uint32_t av[HMAX], F[HMAX];
     int idx[HMAX];
     uint32_t S = (half == 0 && valid) ? nibble_to_high(syn_nib) : 0u;
