@@ -12,10 +12,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _mixed_case(B, Z=32, seed=3, f_target=1.5, scale=8.0, Mb=24, Nb=96):
-    """A 3/6 mixed-degree mother code with per-frame QBER 1-8 % and rates for f_target."""
+def _mixed_case(B, Z=32, seed=3, f_target=1.5, scale=8.0, Mb=24, Nb=96, mask="uniform"):
+    """A 3/6 mixed-degree mother code with per-frame QBER 1-8 % and rates for
+    f_target; ``mask="peg"`` gives rows of 15-16 blocks (the narrow, one-chunk
+    row update and the unrolled stopping test), the uniform draw rows of up to
+    22 (the chunked row update and the looped stopping test)."""
     degs = inputs.mixed_column_degrees(Nb, 0.3, 3, 6, seed)
-    base = inputs.qc_base_matrix(Mb, Nb, Z, degs, seed)
+    make = inputs.peg_base_matrix if mask == "peg" else inputs.qc_base_matrix
+    base = make(Mb, Nb, Z, degs, seed)
     n, m = Nb * Z, Mb * Z
     q = inputs.frame_qbers(B, 0.01, 0.08, seed)
     xa = inputs.alice_keys(B, n, seed)
@@ -51,10 +55,11 @@ def _run(case, max_iter, words=0, ctas=0, frame_list=None, threads=0, stall=0):
     return code, bits.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy()
 
 
+@pytest.mark.parametrize("mask", ["uniform", "peg"])
 @pytest.mark.parametrize("words", [1, 2, 4])
 @pytest.mark.parametrize("scale", [8.0, 1 / 0.29])
-def test_persistent_mixed_rate_bit_exact(words, scale):
-    case = _mixed_case(53, scale=scale)
+def test_persistent_mixed_rate_bit_exact(words, scale, mask):
+    case = _mixed_case(53, scale=scale, mask=mask)
     code, bits, iters, ok = _run(case, 40, words=words)
     ob, oi, oo, _ = orc.decode(case["base"], case["Z"], case["llr"], case["syn_u"], 40)
     assert np.array_equal(ok, oo) and np.array_equal(iters, oi)
@@ -143,14 +148,17 @@ def test_persistent_sizes_not_multiples_of_eight(Z, Mb, Nb):
     assert np.all(bits[:, -1] >> (8 - pad) == 0)
 
 
+@pytest.mark.parametrize("mask", ["uniform", "peg"])
 @pytest.mark.parametrize("words", [1, 2, 4])
 @pytest.mark.parametrize("stall", [2, 6])
-def test_persistent_stall_window_bit_exact(words, stall):
+def test_persistent_stall_window_bit_exact(words, stall, mask):
     """The stall rule (a frame whose count of unsatisfied checks sets no new
     minimum for K iterations stops as a failure): per-lane counts in the
     kernel against the oracle's, through bits, iteration counts and flags.
     A high-QBER, low-efficiency case so that frames stall."""
-    case = _mixed_case(61, seed=31, f_target=1.25, scale=1 / 0.29)
+    case = _mixed_case(61, seed=31, f_target=1.25, scale=1 / 0.29, mask=mask)
+    if mask == "peg":
+        assert int((case["base"] >= 0).sum(axis=1).max()) <= 16
     code, bits, iters, ok = _run(case, 60, words=words, stall=stall)
     ob, oi, oo, _ = orc.decode(case["base"], case["Z"], case["llr"], case["syn_u"], 60, stall_window=stall)
     assert np.array_equal(ok, oo) and np.array_equal(iters, oi)
