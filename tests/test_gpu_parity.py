@@ -138,6 +138,22 @@ def test_decode_ragged_batches_and_group_widths(batch, words):
     _assert_same(g, o)
 
 
+@pytest.mark.parametrize("words", [1, 2, 4])
+def test_decode_peg_mask_full_rows(words):
+    """A PEG mask (rows of 15-16 blocks: every slot of the 8-slot body busy,
+    one guarded chunk) through the batch decoder at every group width,
+    including the multi-word body."""
+    degs = inputs.mixed_column_degrees(96, 0.3, 3, 6, 41)
+    Z = 32
+    base = inputs.peg_base_matrix(24, 96, Z, degs, 41)
+    assert int((base >= 0).sum(axis=1).max()) == 16
+    xa, yb = _frames(base, Z, 29, 0.03, 700 + words)
+    llr, syn_u = _oracle_inputs(base, Z, xa, yb, 0.03)
+    g, o = _decode_both(base, Z, llr, syn_u, 30, words=words)
+    _assert_same(g, o)
+    assert g[2].sum() > 0
+
+
 @pytest.mark.parametrize("Z", [5, 24, 96, 600])
 def test_decode_odd_lifting_sizes(Z):
     """Z not a multiple of the warp size, and Z above the CTA's thread count."""
