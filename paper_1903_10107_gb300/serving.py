@@ -137,19 +137,18 @@ class EpochEngine:
         reqs = [self.queue.popleft() for _ in range(k)]
         pairs = [self.free_pairs.popleft() for _ in range(k)]
         F = 2 * k
-        q = np.empty(F, np.float64)
-        for i, r in enumerate(reqs):
-            # frame 2i: Bob decodes his key against s_A; 2i + 1: Alice decodes hers against s_B
-            self.h_obs[2 * i].numpy()[:] = r.yb
-            self.h_obs[2 * i + 1].numpy()[:] = r.xa
-            self.h_other[2 * i].numpy()[:] = r.xa
-            self.h_other[2 * i + 1].numpy()[:] = r.yb
-            self.h_known[2 * i].numpy()[:] = r.xa
-            self.h_known[2 * i + 1].numpy()[:] = r.xa
-            q[2 * i] = q[2 * i + 1] = r.qber
-            self.h_ns[2 * i] = self.h_ns[2 * i + 1] = r.n_short
-            self.h_np[2 * i] = self.h_np[2 * i + 1] = r.n_punct
-        self.h_mag[:F] = torch.from_numpy(llr_magnitudes(q, self.llr_scale))
+        # frame 2i: Bob decodes his key against s_A; 2i + 1: Alice decodes hers against s_B
+        yb = np.stack([r.yb for r in reqs])
+        xa = np.stack([r.xa for r in reqs])
+        ho, hx, hk = self.h_obs.numpy(), self.h_other.numpy(), self.h_known.numpy()
+        ho[0:F:2], ho[1:F:2] = yb, xa
+        hx[0:F:2], hx[1:F:2] = xa, yb
+        hk[0:F:2], hk[1:F:2] = xa, xa
+        two = lambda attr, dt: np.repeat(np.fromiter((getattr(r, attr) for r in reqs), dt, k), 2)
+        q = two("qber", np.float64)
+        self.h_ns.numpy()[:F] = two("n_short", np.int32)
+        self.h_np.numpy()[:F] = two("n_punct", np.int32)
+        self.h_mag.numpy()[:F] = llr_magnitudes(q, self.llr_scale)
         slots = np.empty(F, np.int64)
         slots[0::2] = 2 * np.asarray(pairs)
         slots[1::2] = 2 * np.asarray(pairs) + 1
@@ -205,30 +204,33 @@ class EpochEngine:
         taken = min(int(self.h_claimed[0]), self._launched)
         self.pending = self.pending[taken:]  # the rest were not reached: next epoch
         iters, ok = self.h_iters.numpy(), self.h_ok.numpy()
-        done = [p for p in self.inflight if iters[2 * p] > 0 and iters[2 * p + 1] > 0]
-        if not done:
+        keys = np.fromiter(self.inflight.keys(), np.int64, len(self.inflight))
+        fin = keys[(iters[2 * keys] > 0) & (iters[2 * keys + 1] > 0)]
+        if fin.size == 0:
             return []
-        R = 2 * len(done)
-        self.h_rows[:R] = torch.from_numpy(np.array([s for p in done for s in (2 * p, 2 * p + 1)], np.int64))
+        R = 2 * fin.size
+        rows = self.h_rows.numpy()
+        rows[0:R:2], rows[1:R:2] = 2 * fin, 2 * fin + 1
         with torch.cuda.stream(self.stream):  # the finished frames' bits, gathered into one copy out
             self.d_rows[:R].copy_(self.h_rows[:R], non_blocking=True)
             torch.index_select(self.out[0], 0, self.d_rows[:R], out=self.d_done_bits[:R])
             self.h_done_bits[:R].copy_(self.d_done_bits[:R], non_blocking=True)
             self.stream.synchronize()
-        bits = self.h_done_bits.numpy()
-        out = []
-        for i, p in enumerate(done):
-            r = self.inflight.pop(p)
-            b0, b1 = bits[2 * i].copy(), bits[2 * i + 1].copy()
-            good = (bool(ok[2 * p]) and np.array_equal(b0, r.xa), bool(ok[2 * p + 1]) and np.array_equal(b1, r.yb))
-            r.ok = good[0] or good[1]
+        bits = self.h_done_bits.numpy()[:R].copy()
+        reqs = [self.inflight.pop(p) for p in fin.tolist()]
+        # a direction succeeds when its decoder matched the syndrome and recovered the other party's key
+        good0 = ok[2 * fin].astype(bool) & (bits[0::2] == np.stack([r.xa for r in reqs])).all(axis=1)
+        good1 = ok[2 * fin + 1].astype(bool) & (bits[1::2] == np.stack([r.yb for r in reqs])).all(axis=1)
+        it0, it1 = iters[2 * fin].tolist(), iters[2 * fin + 1].tolist()
+        g0, g1 = good0.tolist(), good1.tolist()
+        for i, r in enumerate(reqs):
+            r.ok = g0[i] or g1[i]
             r.key_bits = r.n - r.n_punct - r.n_short
-            r.dirs = (good[0], good[1], int(iters[2 * p]), int(iters[2 * p + 1]))
-            r.bits = (b0, b1)
+            r.dirs = (g0[i], g1[i], it0[i], it1[i])
+            r.bits = (bits[2 * i], bits[2 * i + 1])
             r.t_done = now
-            self.free_pairs.append(p)
-            out.append(r)
-        return out
+        self.free_pairs.extend(fin.tolist())
+        return reqs
 
     def idle(self) -> bool:
         return self.event is None and not self.inflight and not self.queue
