@@ -99,11 +99,12 @@ __device__ __forceinline__ void row_update(const RowCtx& C, int r, bool valid, i
     const bool load_l = C.fresh != 0xFFFFFFFFu;
     // Slots are guarded in chunks of CH: a chunk wholly past the walk's count
     // is skipped by one branch, where per-slot guards alone left the idle
-    // slots' instructions to be issued predicated off.  Measured: chunks of 4
-    // are 5.8 % faster on a code with rows of 6-25 edges (13 slots) than
-    // per-slot guards, chunks of 2 or 8 slower there; bodies of at most 8
-    // slots are fastest as one chunk (2.5 % on rows of 15-16 edges).
-    constexpr int CH = HMAX <= 8 ? HMAX : 4;
+    // slots' instructions to be issued predicated off.  Measured on a code
+    // with rows of 6-25 edges (13 slots): chunks of 4 are 5.8 % faster than
+    // per-slot guards, chunks of 3 another 1.4 %, chunks of 2, 6 or 8 slower;
+    // bodies of at most 8 slots are fastest as one chunk (2.5 % on rows of
+    // 15-16 edges).
+    constexpr int CH = HMAX <= 8 ? HMAX : 3;
 #pragma unroll
     for (int c0 = 0; c0 < HMAX; c0 += CH) {
         if (c0 < cnt) {
