@@ -6,7 +6,6 @@ import os
 import re
 
 import numpy as np
-import pytest
 
 from paper_1903_10107_gb300 import native, rate
 from paper_1903_10107_gb300 import inputs

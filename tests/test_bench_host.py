@@ -7,7 +7,6 @@ import shutil
 import types
 
 import pytest
-import torch
 
 import bench
 

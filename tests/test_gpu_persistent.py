@@ -194,7 +194,6 @@ def test_interactive_launch_every_group_width(words, stall):
     """All rounds in one launch (ldpc_reconcile_interactive) at every group
     width: frames failing a round restart in their lane with more bits
     revealed; against the oracle's protocol frame by frame."""
-    import math
     from oracle import protocol as oproto
     from paper_1903_10107_gb300.decoder import QCCode
     case = _mixed_case(47, seed=51, f_target=1.1, scale=1 / 0.29)

@@ -6,7 +6,6 @@ worked example of section 3.3, textbook min-sum as a special case, the
 parity-check invariant, maximum-likelihood decoding by enumeration and the
 closed form of the efficiency.
 """
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,6 @@ was admitted.  Checked: requests wait while their code's pool is full and
 are admitted in arrival order as slots free up; every request completes,
 after it arrived; the pool size follows the memory budget."""
 from collections import deque
-from types import SimpleNamespace
 
 import numpy as np
 import pytest
