@@ -243,7 +243,9 @@ int ldpc_reconcile_interactive(const ldpc_code* code, const uint8_t* bob_bits, c
  * graph capture, and two calls on one handle must not run concurrently
  * (from two host threads) -- they share the copies.  Errors as for
  * ldpc_reconcile_interactive; LDPC_ENOMEM if the copies cannot be
- * allocated. */
+ * allocated.  On an error after the first copy was queued the call still
+ * waits for `stream` before it returns, so the caller's host buffers are
+ * free to reuse whatever the outcome. */
 int ldpc_reconcile_interactive_host(const ldpc_code* code, const uint8_t* bob_bits, const int8_t* llr_mag,
                                     const int32_t* rank, const int32_t* n_short, const int32_t* n_punct,
                                     const uint8_t* known, const uint8_t* target_syndrome, int batch,
