@@ -1,8 +1,9 @@
 """The C oracle's layered decoder against an independent vectorised model at
-the benchmark's own code size: n = 49152 (Z = 512, the PEG mother code of
+the benchmarks' own code sizes: n = 49152 (Z = 512, the PEG mother code of
 rate 0.75 with 3/6 column degrees), frames rate-adapted by puncturing and
-shortening, one batch that decodes (f = 1.36) and one that cannot (f = 1.1).
-Bits, iteration counts and flags must be equal.
+shortening, one batch that decodes (f = 1.36) and one that cannot (f = 1.1);
+and the single-rate n = 40960 code (uniform row draw, rows of 6 to 25
+edges) at its QBER of 3 %.  Bits, iteration counts and flags must be equal.
 
 The model restates sections 2 and 3 over whole layers at once: Eq. 8 with
 saturation, the row sign as the syndrome bit times the product of the
@@ -97,6 +98,22 @@ def _model(base, Z, llr, syn, max_iter):
         if not live.any():
             break
     return (E < 0).astype(np.uint8), iters, ok
+
+
+def _plain_case(name, B):
+    w = inputs.WORKLOADS[name]
+    base = w.base()
+    xa, yb, q = w.frames(B)
+    xa_u, yb_u = inputs.unpack_bits(xa, w.n), inputs.unpack_bits(yb, w.n)
+    return base, w.Z, orc.llr_frames(yb_u, q, scale=w.llr_scale), orc.syndrome(base, w.Z, xa_u)
+
+
+def test_oracle_equals_vectorised_model_on_the_single_rate_code():
+    base, Z, llr, syn = _plain_case("n40960_r080_q03", 2)
+    assert (base >= 0).sum(axis=1).max() >= 20   # long rows: folds of 20+ magnitudes
+    bits, iters, ok = _model(base, Z, llr, syn, 8)
+    ob, oi, ook, _ = orc.decode(base, Z, llr, syn, 8)
+    assert np.array_equal(iters, oi) and np.array_equal(ok, ook) and np.array_equal(bits, ob)
 
 
 @pytest.mark.parametrize("B, f_target, max_iter", [(3, 1.36, 40), (2, 1.1, 12)])
